@@ -1,0 +1,372 @@
+"""Throughput benchmark of the QCT hot path on GB300.
+
+One step = one pass of the whole path over one batch: initial conditions
+(levels + Philox + Eqs. 5-6), adaptive Dormand-Prince integration of every
+trajectory to its stop rule, product analysis, histogram reduction and cross
+sections.  Default workload: the batched H2 + Ca sweep, 16 collision
+energies x 24 impact parameters x 8,192 trajectories = 3,145,728
+trajectories, FP64, in one persistent refill-queue launch.  Inputs (the SoA
+state, ~600 MB) are larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank runs the same
+workload with its own trajectory-id range (weak scaling); the only
+collectives are the timing barrier and a max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# Executed FP64 floating-point operations per attempted integrator step
+# (dadd + dmul + 2 dfma, from ncu sass counters on the profile case: see
+# profiles/).  Includes the six right-hand-side evaluations of the step.
+FP64_FLOP_PER_STEP = None  # set from the ncu capture; None -> reported as null
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "plain", "mixed"])
+    ap.add_argument("--per-cell", type=int, default=8192,
+                    help="sweep: trajectories per (E, b) cell")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="use a stratified subset of this many lanes (profiling runs)")
+    ap.add_argument("--max-steps", type=int, default=1_000_000)
+    ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--cpu-per-cell", type=int, default=8,
+                    help="oracle sample for cpu_baseline: lanes per cell")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(args):
+    from paper_2304_02731_gb300 import workloads as W
+    if args.workload == "sweep":
+        wl = W.sweep_h2_ca(per_cell=args.per_cell)
+    elif args.workload == "plain":
+        wl = W.plain_h2_ca()
+    else:
+        wl = W.mixed_ca_h()
+    if args.lanes and args.lanes < wl.n:
+        per = max(1, args.lanes // wl.n_cells)
+        wl = wl.take(W.stratified(wl, per))
+    return wl
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_chunk(payload):
+    import oracle as O
+    specs, sid, E, b, v, j, R0, seed, ids, integ_kw = payload
+    systems = [O.system_from_spec(s) for s in specs]
+    integ = O.make_integ(**integ_kw)
+    t0 = time.perf_counter()
+    n = 0
+    for k in range(len(E)):
+        O.run_lanes(systems, sid[k:k + 1], E[k:k + 1], b[k:k + 1], v[k:k + 1], j[k:k + 1], R0,
+                    seed, integ, id_offset=int(ids[k]))
+        n += 1
+    return n, time.perf_counter() - t0
+
+
+def oracle_rate(wl, per_cell: int, idx_offset: int = 0):
+    """Time the oracle as it stands on a stratified sample of the workload,
+    one single-threaded oracle process per host core.  Returns
+    (trajectories/s, cores, sample description, lanes)."""
+    import multiprocessing as mp
+    from paper_2304_02731_gb300 import workloads as W
+    import oracle as O
+    O.build()
+    idx = W.stratified(wl, per_cell + idx_offset)
+    if idx_offset:
+        # skip the first idx_offset lanes of every cell (a fresh sample per step)
+        keep = []
+        starts = np.flatnonzero(np.r_[True, wl.cell[idx][1:] != wl.cell[idx][:-1]])
+        for s0, s1 in zip(starts, list(starts[1:]) + [len(idx)]):
+            keep.extend(idx[s0 + idx_offset:s1])
+        idx = np.asarray(keep)
+    cores = os.cpu_count() or 1
+    ids = wl.id_offset + idx
+    chunks = np.array_split(np.arange(len(idx)), cores)
+    payloads = []
+    for c in chunks:
+        if len(c) == 0:
+            continue
+        sel = idx[c]
+        payloads.append((wl.systems, wl.sys_id[sel], wl.E[sel], wl.b[sel], wl.v[sel],
+                         wl.j[sel], wl.R0, wl.seed, ids[c], dict(wl.integ)))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(len(payloads)) as pool:
+        res = pool.map(_oracle_chunk, payloads)
+    wall = time.perf_counter() - t0
+    n = sum(r[0] for r in res)
+    return n / wall, len(payloads), n, wall
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = make_workload(args)
+    for w in range(args.warmup):
+        oracle_rate(wl, 1, idx_offset=w)
+    rates, walls, ns = [], [], []
+    for k in range(args.steps):
+        r, cores, n, wall = oracle_rate(wl, args.cpu_per_cell // 2 or 1,
+                                        idx_offset=args.warmup + k)
+        rates.append(r)
+        walls.append(wall)
+        ns.append(n)
+    value = sum(ns) / sum(walls)
+    sample = (f"{ns[0]} lanes per step: {args.cpu_per_cell // 2 or 1} per (E, b) cell of the "
+              f"{wl.name} workload, one single-threaded FP64 oracle process per core")
+    line = {"impl": "reference", "metric": "trajectories/s (H2+Ca, FP64 RK45)",
+            "value": value, "unit": "trajectories/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name, "trajectories": wl.n},
+            "cpu_baseline": {"value": value, "unit": "trajectories/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "trajectories/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2304_02731_gb300 import build as B
+    B.build()
+    from paper_2304_02731_gb300 import qcams as Q
+
+    wl = make_workload(args)
+    wl.id_offset = rank * wl.n          # weak scaling: each rank its own trajectory ids
+    integ = Q.make_integ(**wl.integ, persistent=bool(args.persistent), block=args.block,
+                         max_steps=args.max_steps)
+    batch = Q.Batch.empty(wl.n, dev, sys_id=wl.sys_id, cell=wl.cell, keep_u=False)
+    E_d = torch.as_tensor(wl.E, device=dev)
+    b_d = torch.as_tensor(wl.b, device=dev)
+    v_d = torch.as_tensor(wl.v, device=dev)
+    j_d = torch.as_tensor(wl.j, device=dev)
+    hist = torch.empty(wl.n_cells * Q.H_STRIDE, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(finalize=False):
+        Q.init_states(wl.systems, batch, E_d, b_d, v_d, j_d, wl.R0, wl.seed, wl.id_offset)
+        Q.run_batch(wl.systems, batch, integ)
+        return Q.reduce_xsec(batch, wl.n_cells, wl.cell_b, wl.cell_w, wl.cell_group,
+                             wl.n_groups, hist_out=hist, finalize=finalize)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    integ_ms, steps_total, rhs_total = [], 0, 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+        st = Q.last_run_stats()          # synchronises; read after each step's run
+        integ_ms.append(st["integrate_ms"])
+        steps_total += st["steps"]
+        rhs_total += st["rhs"]
+    e1.record(stream)
+    barrier()
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * wl.n * args.steps / (ms_max * 1e-3)
+
+    # one finalised pass for the record (cross sections), outside the timing
+    _, cells, groups = step(finalize=True)
+    torch.cuda.synchronize()
+    hb = batch.host()
+
+    # end-to-end through the public API with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a, dt: torch.as_tensor(a, dtype=dt).pin_memory()
+        hE, hb_, hv, hj = (pin(wl.E, torch.float64), pin(wl.b, torch.float64),
+                           pin(wl.v, torch.int32), pin(wl.j, torch.int32))
+        hsid, hcell = pin(wl.sys_id, torch.int32), pin(wl.cell, torch.int32)
+        hhist = torch.empty(wl.n_cells * Q.H_STRIDE, dtype=torch.int64).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            batch.sys_id.copy_(hsid, non_blocking=True)
+            batch.cell.copy_(hcell, non_blocking=True)
+            E_d.copy_(hE, non_blocking=True)
+            b_d.copy_(hb_, non_blocking=True)
+            v_d.copy_(hv, non_blocking=True)
+            j_d.copy_(hj, non_blocking=True)
+            step()
+            hhist.copy_(hist, non_blocking=True)
+        barrier()
+        wall = time.perf_counter() - t0
+        h2d = sum(x.numel() * x.element_size() for x in (hE, hb_, hv, hj, hsid, hcell))
+        e2e = {"value": world * wl.n * args.steps / wall, "unit": "trajectories/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hhist.numel() * 8)}
+
+    # roofline of the dominant kernel (the integrator): FP64 pipe
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    fp64_peak = Q.fma_peak(64)          # measured here: MEASURED_PEAKS.json has no FP64 figure
+    avg_integ_ms = float(np.mean(integ_ms))
+    steps_per_launch = steps_total / max(1, args.steps)
+    roofline = {"bound": "alu", "unit": "TFLOP/s",
+                "peak": fp64_peak / 1e12,
+                "peak_source": "measured DFMA chain microbenchmark (qcams_fma_peak), this run",
+                "traffic": None}
+    if FP64_FLOP_PER_STEP:
+        ach = FP64_FLOP_PER_STEP * steps_per_launch / (avg_integ_ms * 1e-3)
+        roofline.update(achieved=ach / 1e12, frac=ach / fp64_peak,
+                        flop_per_step=FP64_FLOP_PER_STEP)
+    else:
+        roofline.update(achieved=None, frac=None)
+    roofline.update(steps_per_launch=steps_per_launch, integrate_ms=avg_integ_ms,
+                    rhs_per_launch=rhs_total / max(1, args.steps))
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        r, cores, n, wall = oracle_rate(wl, args.cpu_per_cell)
+        cpu = {"value": r, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n} lanes ({args.cpu_per_cell} per (E, b) cell), {wall:.1f} s wall "
+                         f"on {cores} host cores"}
+
+    cls_counts = np.bincount(hb["cls"], minlength=6).tolist()
+    line = {
+        "metric": "trajectories/s (H2+Ca, FP64 RK45)", "value": value,
+        "unit": "trajectories/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "trajectories_per_gpu": wl.n,
+                   "launch": "persistent refill queue" if args.persistent else "one thread/lane",
+                   "rtol": wl.integ["rtol"], "atol": wl.integ["atol"],
+                   "l2": "inputs larger than L2 (SoA state > 129 MB)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": 8 * args.steps,
+        "clocks": clock_info,
+        "outcomes": {"cls_counts_Q_RAC_RBC_D_AMBIG_FAIL": cls_counts,
+                     "sigma_first_group": groups[0, :, 0].tolist() if groups is not None and
+                     len(groups) else None},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,1055 @@
+// C ABI of the QCT library (include/qcams.h) and the kernels of the path
+// other than the integrator: potential shapes, Bohr-Sommerfeld levels,
+// initial conditions, product analysis and histogram reduction.
+//
+// Physics: Koots & Perez-Rios, PyQCAMS (Comput. Phys. Commun.).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "qcams.h"
+#include "qcams_device.cuh"
+#include "qcams_internal.h"
+
+namespace qcams {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kAmu = 1822.888486209;   // electron masses per unified atomic mass unit
+constexpr int kMaxDevices = 64;
+constexpr int kMaxLevelsReq = 65536;
+constexpr int kMaxCells = 65536;
+
+// Gauss-Legendre rules on [-1, 1] (positive half of the symmetric nodes):
+// 64 points for the per-lane action integral, 128 for the level solver.
+constexpr int kGL64 = 64, kGL128 = 128;
+__constant__ double cGL64x[kGL64 / 2], cGL64w[kGL64 / 2];
+__constant__ double cGL128x[kGL128 / 2], cGL128w[kGL128 / 2];
+
+std::mutex g_mutex;
+Ctx* g_ctx[kMaxDevices] = {nullptr};
+
+// Gauss-Legendre nodes and weights by Newton iteration on P_n(x), with the
+// three-term recurrence for P_n and the derivative identity
+// (x^2 - 1) P_n' = n (x P_n - P_{n-1}); w = 2 / ((1 - x^2) P_n'^2).
+void gauss_legendre(int n, double* x_pos, double* w_pos) {
+  for (int i = 0; i < n / 2; ++i) {
+    double x = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    x_pos[i] = x;
+    w_pos[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+cudaError_t ctx_get(Ctx** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  if (g_ctx[dev]) {
+    *out = g_ctx[dev];
+    return cudaSuccess;
+  }
+  Ctx* c = new Ctx();
+  c->device = dev;
+  e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMalloc(&c->shapes, sizeof(DevShape) * QCAMS_MAX_SYS * 3);
+  if (e == cudaSuccess) e = cudaMalloc(&c->levels, sizeof(DevLevel) * kLevelCells);
+  if (e == cudaSuccess) e = cudaMalloc(&c->level_flag, kLevelCells);
+  if (e == cudaSuccess) e = cudaMalloc(&c->counters, sizeof(unsigned long long) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&c->req_out, sizeof(qcams_level) * kMaxLevelsReq);
+  if (e == cudaSuccess) e = cudaMalloc(&c->req_in, sizeof(int32_t) * 3 * kMaxLevelsReq);
+  if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned long long) * 8);
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+  if (e == cudaSuccess) {
+    double x64[kGL64 / 2], w64[kGL64 / 2], x128[kGL128 / 2], w128[kGL128 / 2];
+    gauss_legendre(kGL64, x64, w64);
+    gauss_legendre(kGL128, x128, w128);
+    e = cudaMemcpyToSymbol(cGL64x, x64, sizeof(x64));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGL64w, w64, sizeof(w64));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGL128x, x128, sizeof(x128));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGL128w, w128, sizeof(w128));
+  }
+  if (e != cudaSuccess) {
+    cudaFree(c->shapes); cudaFree(c->levels); cudaFree(c->level_flag); cudaFree(c->counters);
+    cudaFree(c->req_out); cudaFree(c->req_in);
+    for (int k = 0; k < 4; ++k) if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+    return e;
+  }
+  g_ctx[dev] = c;
+  *out = c;
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side validation and set-up of the per-system constants.
+// ---------------------------------------------------------------------------
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int make_devpair(const qcams_pair& in, DevPair* out) {
+  std::memset(out, 0, sizeof(*out));
+  out->kind = in.kind;
+  for (int i = 0; i < 5; ++i) {
+    if (!std::isfinite(in.p[i])) return QCAMS_E_INVALID;
+    out->p[i] = in.p[i];
+  }
+  const double* p = in.p;
+  switch (in.kind) {
+    case QCAMS_MORSE:
+      if (!finite_pos(p[0]) || !finite_pos(p[1]) || !finite_pos(p[2])) return QCAMS_E_INVALID;
+      out->c0 = p[2];
+      out->c1 = p[2] * p[1];
+      out->c2 = 2.0 * p[2] * p[0];
+      out->c3 = p[0];
+      out->r_scale = p[1];
+      return QCAMS_OK;
+    case QCAMS_LJ: {
+      double m = p[0], n = p[1];
+      if (m != std::floor(m) || n != std::floor(n)) return QCAMS_E_INVALID;
+      if (!(n >= 3 && m > n && m <= QCAMS_LJ_MAX_POW)) return QCAMS_E_INVALID;
+      if (!finite_pos(p[2]) || !finite_pos(p[3])) return QCAMS_E_INVALID;
+      out->m = (int)m;
+      out->n = (int)n;
+      out->c0 = p[2];
+      out->c1 = p[3];
+      out->c2 = m * p[2];
+      out->c3 = n * p[3];
+      out->r_scale = p[4] > 0 ? p[4] : std::pow(m * p[2] / (n * p[3]), 1.0 / (m - n));
+      return QCAMS_OK;
+    }
+    case QCAMS_BUCK:
+      if (!finite_pos(p[0]) || !finite_pos(p[1]) || !finite_pos(p[2])) return QCAMS_E_INVALID;
+      out->c0 = p[0];
+      out->c1 = p[1];
+      out->c2 = p[0] * p[1];
+      out->c3 = 6.0 * p[2];
+      out->c4 = p[2];
+      out->r_scale = p[3] > 0 ? p[3] : 1.0;
+      return QCAMS_OK;
+    default:
+      return QCAMS_E_INVALID;
+  }
+}
+
+int make_sysset(const qcams_system* sys, int32_t n_sys, SysSet* out) {
+  if (!sys || n_sys < 1 || n_sys > QCAMS_MAX_SYS) return QCAMS_E_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  out->n = n_sys;
+  for (int s = 0; s < n_sys; ++s) {
+    const qcams_system& in = sys[s];
+    DevSys& d = out->s[s];
+    double mA = in.mass[0], mB = in.mass[1], mC = in.mass[2];
+    if (!finite_pos(mA) || !finite_pos(mB) || !finite_pos(mC)) return QCAMS_E_INVALID;
+    d.mu12 = mA * mB / (mA + mB);
+    d.mu123 = mC * (mA + mB) / (mA + mB + mC);
+    d.inv_mu12 = 1.0 / d.mu12;
+    d.inv_mu123 = 1.0 / d.mu123;
+    d.cA = mB / (mA + mB);
+    d.cB = mA / (mA + mB);
+    d.mu_pair[0] = mA * mB / (mA + mB);
+    d.mu_pair[1] = mB * mC / (mB + mC);
+    d.mu_pair[2] = mC * mA / (mC + mA);
+    for (int k = 0; k < 3; ++k) {
+      int rc = make_devpair(in.pair[k], &d.pair[k]);
+      if (rc != QCAMS_OK) return rc;
+    }
+  }
+  return QCAMS_OK;
+}
+
+int make_integ_params(const qcams_integ* in, IntegParams* ip) {
+  if (!in) return QCAMS_E_INVALID;
+  if (in->fixed_step) {
+    if (!finite_pos(in->h_fixed) || in->max_steps < 0) return QCAMS_E_INVALID;
+  } else {
+    if (!finite_pos(in->rtol) || !(in->atol >= 0) || !std::isfinite(in->atol))
+      return QCAMS_E_INVALID;
+    if (!finite_pos(in->r_stop) || !finite_pos(in->t_stop) || in->max_steps < 1)
+      return QCAMS_E_INVALID;
+  }
+  if (in->precision != 64 && in->precision != 0) return QCAMS_E_INVALID;
+  if (in->block < 0 || in->block > 1024 || in->blocks_per_sm < 0) return QCAMS_E_INVALID;
+  ip->rtol = in->rtol;
+  ip->atol = in->atol;
+  ip->r_stop2 = in->r_stop * in->r_stop;
+  ip->t_stop = in->t_stop;
+  ip->h_fixed = in->h_fixed;
+  ip->max_steps = in->max_steps;
+  ip->fixed_step = in->fixed_step ? 1 : 0;
+  return QCAMS_OK;
+}
+
+int check_batch(const qcams_batch* b, bool need_outputs) {
+  if (!b || b->n < 0) return QCAMS_E_INVALID;
+  if (b->n == 0) return QCAMS_OK;
+  if (b->n > (int64_t)1 << 40) return QCAMS_E_CAPACITY;
+  if (!b->sys_id || !b->t || !b->h || !b->t_scale || !b->E0 || !b->Ecol || !b->status ||
+      !b->nsteps || !b->nrej)
+    return QCAMS_E_INVALID;
+  for (int k = 0; k < 12; ++k)
+    if (!b->y[k]) return QCAMS_E_INVALID;
+  if (need_outputs && (!b->cls || !b->dE || !b->vprime || !b->jprime || !b->gbw || !b->vt ||
+                       !b->jt))
+    return QCAMS_E_INVALID;
+  return QCAMS_OK;
+}
+
+DevBatch dev_batch(const qcams_batch* b) {
+  DevBatch d;
+  d.n = b->n;
+  d.sys_id = b->sys_id;
+  d.cell = b->cell;
+  d.isw = b->isw;
+  for (int k = 0; k < 12; ++k) d.y[k] = b->y[k];
+  d.t = b->t;
+  d.h = b->h;
+  d.t_scale = b->t_scale;
+  d.E0 = b->E0;
+  d.Ecol = b->Ecol;
+  for (int k = 0; k < 4; ++k) d.u[k] = b->u[k];
+  d.status = b->status;
+  d.cls = b->cls;
+  d.nsteps = b->nsteps;
+  d.nrej = b->nrej;
+  d.dE = b->dE;
+  d.vprime = b->vprime;
+  d.jprime = b->jprime;
+  d.gbw = b->gbw;
+  d.vt = b->vt;
+  d.jt = b->jt;
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Potential shapes (once per call): well bottom r_eq, Buckingham short-range
+// maximum r_b, and the maximum of g(r) = r^3 V'(r) beyond r_eq.
+// ---------------------------------------------------------------------------
+__device__ DevShape pair_shape(const DevPair& q) {
+  DevShape sh{};
+  sh.ok = 0;
+  if (q.kind == QCAMS_MORSE) {
+    sh.r_eq = q.p[1];
+  } else if (q.kind == QCAMS_LJ) {
+    sh.r_eq = pow(q.c2 / q.c3, 1.0 / (q.m - q.n));
+  } else {
+    // Buckingham: V' > 0 at short range (collapse side), then the maximum
+    // r_b (V' from + to -), then the well bottom r_eq (V' from - to +).
+    // Scan a logarithmic grid over [0.02, 200] bohr for the two changes.
+    const int N = 4096;
+    const double lo = 0.02, hi = 200.0, dl = log(hi / lo) / N;
+    double pr = lo, pv = pot_dV(q, lo);
+    double rb_a = 0, rb_b = 0, re_a = 0, re_b = 0;
+    bool got_b = false, got_e = false;
+    for (int k = 1; k <= N && !got_e; ++k) {
+      double r = lo * exp(dl * k), dv = pot_dV(q, r);
+      if (!got_b && pv > 0 && dv <= 0) { got_b = true; rb_a = pr; rb_b = r; }
+      else if (got_b && pv < 0 && dv >= 0) { got_e = true; re_a = pr; re_b = r; }
+      pr = r; pv = dv;
+    }
+    if (!got_b || !got_e) return sh;
+    auto f = [&](double r) { return pot_dV(q, r); };
+    sh.r_b = illinois(f, rb_a, rb_b, f(rb_a), f(rb_b));
+    sh.r_b2 = sh.r_b * sh.r_b;
+    sh.r_eq = illinois(f, re_a, re_b, f(re_a), f(re_b));
+  }
+  // bracket the maximum of g beyond r_eq by geometric steps, then golden
+  // section (g is unimodal on (r_eq, inf) for the three potential kinds)
+  double a = sh.r_eq, m = sh.r_eq * 1.5, b = m * 1.5;
+  double gm = gfun(q, m), gb = gfun(q, b);
+  for (int it = 0; it < 200 && gb >= gm; ++it) {
+    a = m; m = b; gm = gb;
+    b = m * 1.5;
+    gb = gfun(q, b);
+  }
+  const double gr = 0.6180339887498949;
+  double x1 = b - gr * (b - a), x2 = a + gr * (b - a);
+  double f1 = gfun(q, x1), f2 = gfun(q, x2);
+  for (int it = 0; it < 200 && (b - a) > 1e-12 * b; ++it) {
+    if (f1 < f2) { a = x1; x1 = x2; f1 = f2; x2 = a + gr * (b - a); f2 = gfun(q, x2); }
+    else { b = x2; x2 = x1; f2 = f1; x1 = b - gr * (b - a); f1 = gfun(q, x1); }
+  }
+  sh.r_peak = 0.5 * (a + b);
+  sh.g_max = gfun(q, sh.r_peak);
+  sh.ok = (sh.g_max > 0.0 && sh.r_eq > 0.0) ? 1 : 0;
+  return sh;
+}
+
+__global__ void k_pair_shapes(SysSet sys, DevShape* out) {
+  int t = threadIdx.x;
+  if (t >= sys.n * 3) return;
+  out[t] = pair_shape(sys.s[t / 3].pair[t % 3]);
+}
+
+// Well of the effective potential V + L2/(2 mu r^2): bottom r_min and outer
+// maximum r_top (r_top = +inf and threshold 0 when L2 = 0).  Returns false
+// when L2/mu >= g_max (no well).
+__device__ bool eff_well(const DevPair& q, const DevShape& sh, double mu, double L2,
+                         double* r_min, double* r_top, double* thr) {
+  if (L2 <= 0.0) {
+    *r_min = sh.r_eq;
+    *r_top = INFINITY;
+    *thr = 0.0;
+    return true;
+  }
+  const double c = L2 / mu;
+  if (!(c < sh.g_max)) return false;
+  auto G = [&](double r) { return gfun(q, r) - c; };
+  *r_min = illinois(G, sh.r_eq, sh.r_peak, -c, sh.g_max - c);
+  double a = sh.r_peak, b = 2.0 * sh.r_peak, gb = G(b);
+  for (int it = 0; it < 60 && gb >= 0.0; ++it) {
+    a = b;
+    b *= 2.0;
+    gb = G(b);
+  }
+  if (gb >= 0.0) {  // barrier beyond reach (vanishing L): threshold 0
+    *r_top = INFINITY;
+    *thr = 0.0;
+    return true;
+  }
+  *r_top = illinois(G, a, b, G(a), gb);
+  *thr = veff(q, mu, L2, *r_top);
+  return true;
+}
+
+// Turning points of E = V_eff inside the well.
+__device__ bool turning_points(const DevPair& q, const DevShape& sh, double mu, double L2, double E,
+                               double r_min, double r_top, double* rm, double* rp) {
+  auto f = [&](double r) { return veff(q, mu, L2, r) - E; };
+  double fmin_ = f(r_min);
+  if (!(fmin_ < 0.0)) return false;
+  // inner: V_eff rises steeply toward small r (Buckingham: up to r_b)
+  double lo, flo;
+  if (q.kind == QCAMS_BUCK) {
+    lo = sh.r_b;
+    flo = f(lo);
+    if (!(flo > 0.0)) return false;
+  } else {
+    lo = 0.5 * r_min;
+    flo = f(lo);
+    for (int it = 0; it < 60 && flo <= 0.0; ++it) {
+      lo *= 0.5;
+      flo = f(lo);
+    }
+    if (!(flo > 0.0)) return false;
+  }
+  *rm = illinois(f, lo, r_min, flo, fmin_);
+  double hi, fhi;
+  if (isfinite(r_top)) {
+    hi = r_top;
+    fhi = f(hi);
+  } else {
+    hi = 2.0 * r_min;
+    fhi = f(hi);
+    for (int it = 0; it < 60 && fhi <= 0.0; ++it) {
+      hi *= 2.0;
+      fhi = f(hi);
+    }
+  }
+  if (!(fhi > 0.0)) return false;
+  *rp = illinois(f, r_min, hi, fmin_, fhi);
+  return true;
+}
+
+// Action and period integrals by Gauss-Legendre in s after r = c + d sin(s)
+// (the mapped integrands are smooth on the closed interval):
+//   I_act = int sqrt(E - V_eff) dr,  I_per = int dr / sqrt(E - V_eff).
+template <int NG>
+__device__ void action_period(const DevPair& q, double mu, double L2, double E, double rm,
+                              double rp, double* act, double* per) {
+  const double c = 0.5 * (rp + rm), d = 0.5 * (rp - rm);
+  double sa = 0.0, sp = 0.0;
+  for (int k = 0; k < NG / 2; ++k) {
+    const double x = (NG == kGL64) ? cGL64x[k] : cGL128x[k];
+    const double w = (NG == kGL64) ? cGL64w[k] : cGL128w[k];
+    double sn, cs;
+    sincospi(0.5 * x, &sn, &cs);
+#pragma unroll
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      const double r = sgn ? c - d * sn : c + d * sn;
+      const double g = E - veff(q, mu, L2, r);
+      if (g > 0.0) {
+        const double sq = sqrt(g);
+        sa += w * sq * d * cs;
+        sp += w * d * cs / sq;
+      }
+    }
+  }
+  *act = 0.5 * kPi * sa;
+  *per = 0.5 * kPi * sp;
+}
+
+// Bohr-Sommerfeld level: solve v(E) = -1/2 + sqrt(2 mu)/pi I_act(E) = v by a
+// Newton iteration safeguarded by bisection, with dv/dE = tau(E) / (2 pi)
+// and tau = sqrt(2 mu) I_per (Sec. 2.1, Eq. 7; Sec. 2.2, Eq. 10).
+__device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu, int v, int j) {
+  DevLevel L{};
+  L.ok = 0;
+  if (!sh.ok) return L;
+  const double L2 = (double)j * (double)(j + 1);
+  double r_min, r_top, Etop;
+  if (!eff_well(q, sh, mu, L2, &r_min, &r_top, &Etop)) return L;
+  const double Vmin = veff(q, mu, L2, r_min);
+  const double s2mu = sqrt(2.0 * mu);
+  double lo = Vmin, hi = Etop - 1e-10 * (Etop - Vmin);
+  double rm, rp, act, per;
+  if (!turning_points(q, sh, mu, L2, hi, r_min, r_top, &rm, &rp)) return L;
+  action_period<kGL128>(q, mu, L2, hi, rm, rp, &act, &per);
+  if (-0.5 + s2mu / kPi * act < v) return L;
+  // harmonic first guess
+  double k2 = pot_d2V(q, r_min) + 3.0 * L2 / (mu * r_min * r_min * r_min * r_min);
+  double E = Vmin + (v + 0.5) * sqrt(fmax(k2, 0.0) / mu);
+  if (!(E > lo && E < hi)) E = 0.5 * (lo + hi);
+  bool ok = false;
+  for (int it = 0; it < 200; ++it) {
+    if (!turning_points(q, sh, mu, L2, E, r_min, r_top, &rm, &rp)) break;
+    action_period<kGL128>(q, mu, L2, E, rm, rp, &act, &per);
+    const double f = -0.5 + s2mu / kPi * act - v;
+    if (f < 0) lo = E; else hi = E;
+    double En = E - f * 2.0 * kPi / (s2mu * per);
+    if (!(En > lo && En < hi)) En = 0.5 * (lo + hi);
+    if (fabs(En - E) <= 2e-16 * fmax(fabs(E), fabs(Vmin)) || hi - lo <= 4e-16 * fabs(Vmin)) {
+      E = En;
+      ok = true;
+      break;
+    }
+    E = En;
+  }
+  if (!ok) return L;
+  if (!turning_points(q, sh, mu, L2, E, r_min, r_top, &rm, &rp)) return L;
+  action_period<kGL128>(q, mu, L2, E, rm, rp, &act, &per);
+  L.E = E;
+  L.r_minus = rm;
+  L.r_plus = rp;
+  L.tau = s2mu * per;
+  L.ok = 1;
+  return L;
+}
+
+// Mark the (sys, v, j) levels the lanes need.
+__global__ void k_mark_levels(int64_t n, const int32_t* sys_id, const int32_t* v,
+                              const int32_t* j, int n_sys, uint8_t* flag) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int s = sys_id[i], vv = v[i], jj = j[i];
+  if (s < 0 || s >= n_sys || vv < 0 || vv > QCAMS_V_MAX || jj < 0 || jj > QCAMS_J_MAX) return;
+  flag[level_index(s, vv, jj)] = 1;
+}
+
+// Solve every marked level of the dense table (one thread per table cell).
+__global__ void k_solve_levels(SysSet sys, const DevShape* shapes, const uint8_t* flag,
+                               DevLevel* levels) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kLevelCells || !flag[idx]) return;
+  int s = idx / (kLevelV * kLevelJ);
+  int v = (idx / kLevelJ) % kLevelV;
+  int j = idx % kLevelJ;
+  if (s >= sys.n) return;
+  levels[idx] = solve_level(sys.s[s].pair[0], shapes[s * 3], sys.s[s].mu_pair[0], v, j);
+}
+
+// Levels for an explicit request list (qcams_levels).
+__global__ void k_levels_list(SysSet sys, const DevShape* shapes, const int32_t* req, int n,
+                              qcams_level* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int s = req[3 * k], v = req[3 * k + 1], j = req[3 * k + 2];
+  DevLevel L = solve_level(sys.s[s].pair[0], shapes[s * 3], sys.s[s].mu_pair[0], v, j);
+  qcams_level o;
+  o.E = L.E; o.r_minus = L.r_minus; o.r_plus = L.r_plus; o.tau = L.tau; o.ok = L.ok; o.pad = 0;
+  out[k] = o;
+}
+
+// Total energy (Eq. 2).
+__device__ double hamiltonian(const DevSys& S, const double* y) {
+  double T = (y[6] * y[6] + y[7] * y[7] + y[8] * y[8]) * (0.5 * S.inv_mu12) +
+             (y[9] * y[9] + y[10] * y[10] + y[11] * y[11]) * (0.5 * S.inv_mu123);
+  double V = 0.0;
+  double r[3][3];
+  for (int a = 0; a < 3; ++a) {
+    r[0][a] = y[a];
+    r[1][a] = y[3 + a] - S.cB * y[a];
+    r[2][a] = y[3 + a] + S.cA * y[a];
+  }
+  for (int k = 0; k < 3; ++k)
+    V += pot_V(S.pair[k], sqrt(r[k][0] * r[k][0] + r[k][1] * r[k][1] + r[k][2] * r[k][2]));
+  return T + V;
+}
+
+// Initial conditions (Sec. 2.1, Eqs. 5-6).
+__global__ void k_init(SysSet sys, const DevLevel* levels, const double* E_col, const double* b,
+                       const int32_t* v, const int32_t* j, double R0, uint64_t seed,
+                       uint64_t id_offset, const double* u0, const double* u1, const double* u2,
+                       const double* u3, DevBatch B) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= B.n) return;
+  int st = QCAMS_LANE_READY;
+  int s = B.sys_id[i], vv = v[i], jj = j[i];
+  double E = E_col[i], bb = b[i];
+  B.t[i] = 0.0;
+  B.h[i] = 0.0;
+  B.nsteps[i] = 0;
+  B.nrej[i] = 0;
+  B.Ecol[i] = E;
+  if (s < 0 || s >= sys.n || !(E > 0.0) || !(bb >= 0.0)) st = QCAMS_LANE_INVALID;
+  else if (vv < 0 || vv > QCAMS_V_MAX || jj < 0 || jj > QCAMS_J_MAX) st = QCAMS_LANE_NO_LEVEL;
+  DevLevel L{};
+  if (st == QCAMS_LANE_READY) {
+    L = levels[level_index(s, vv, jj)];
+    if (!L.ok) st = QCAMS_LANE_NO_LEVEL;
+  }
+  double u[4];
+  if (u0) {
+    u[0] = u0[i]; u[1] = u1[i]; u[2] = u2[i]; u[3] = u3[i];
+  } else {
+    const uint64_t id = id_offset + (uint64_t)i;
+    uint4 w = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), 0u, 0u),
+                            make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    u[0] = u01(w.x); u[1] = u01(w.y); u[2] = u01(w.z); u[3] = u01(w.w);
+  }
+  if (B.u[0])
+    for (int k = 0; k < 4; ++k) B.u[k][i] = u[k];
+  double y[12];
+  for (int k = 0; k < 12; ++k) y[k] = 0.0;
+  double ts = 0.0, E0 = 0.0;
+  if (st == QCAMS_LANE_READY) {
+    const DevSys& S = sys.s[s];
+    const double cth = 2.0 * u[0] - 1.0;
+    const double sth = sqrt(fmax(0.0, 1.0 - cth * cth));
+    double sph, cph, seta, ceta;
+    sincospi(2.0 * u[1], &sph, &cph);
+    sincospi(2.0 * u[2], &seta, &ceta);
+    const double chi = u[3];
+    const double rp = L.r_plus;
+    const double P1 = sqrt((double)jj * (double)(jj + 1)) / rp;
+    y[0] = rp * sth * cph;
+    y[1] = rp * sth * sph;
+    y[2] = rp * cth;
+    y[6] = P1 * (sph * ceta - cth * cph * seta);
+    y[7] = P1 * (-cph * ceta - cth * sph * seta);
+    y[8] = P1 * (sth * seta);
+    const double P2 = sqrt(2.0 * S.mu123 * E);
+    const double R = R0 + chi * P2 * L.tau * S.inv_mu123;
+    if (!(R > bb)) {
+      st = QCAMS_LANE_INVALID;
+    } else {
+      y[3] = 0.0;
+      y[4] = bb;
+      y[5] = -sqrt((R - bb) * (R + bb));
+      y[11] = P2;
+      ts = R * S.mu123 / P2;
+      E0 = hamiltonian(S, y);
+    }
+  }
+  for (int k = 0; k < 12; ++k) B.y[k][i] = y[k];
+  B.t_scale[i] = ts;
+  B.E0[i] = E0;
+  B.status[i] = (uint8_t)st;
+}
+
+// ---------------------------------------------------------------------------
+// Product analysis (Sec. 2.2).
+// ---------------------------------------------------------------------------
+struct PairBound {
+  bool bound;
+  double r_min, r_top;
+};
+
+__device__ PairBound pair_bound(const DevPair& q, const DevShape& sh, double mu, double L2,
+                                double E, double r) {
+  PairBound pb{false, 0.0, INFINITY};
+  double thr;
+  if (!sh.ok || !eff_well(q, sh, mu, L2, &pb.r_min, &pb.r_top, &thr)) return pb;
+  bool b = E < thr && r < pb.r_top;
+  if (q.kind == QCAMS_BUCK) b = b && r > sh.r_b && E < veff(q, mu, L2, sh.r_b);
+  pb.bound = b;
+  return pb;
+}
+
+__global__ void k_analyze(SysSet sys, const DevShape* shapes, double gb_sigma, DevBatch B) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= B.n) return;
+  const int st = B.status[i];
+  const int sid = B.sys_id[i];
+  double y[12];
+  for (int k = 0; k < 12; ++k) y[k] = B.y[k][i];
+  int cls = QCAMS_CLS_FAIL;
+  double vp = 0.0, jp = 0.0, w = 0.0, dE = 0.0;
+  int vt = 0, jt = 0;
+  if (sid >= 0 && sid < sys.n && st != QCAMS_LANE_NO_LEVEL && st != QCAMS_LANE_INVALID)
+    dE = hamiltonian(sys.s[sid], y) - B.E0[i];
+  if ((st == QCAMS_LANE_DONE_RSTOP || st == QCAMS_LANE_DONE_TMAX) && sid >= 0 && sid < sys.n) {
+    const DevSys& S = sys.s[sid];
+    double r[3][3], vv[3][3];
+    for (int a = 0; a < 3; ++a) {
+      const double v1 = y[6 + a] * S.inv_mu12, v2 = y[9 + a] * S.inv_mu123;
+      r[0][a] = y[a];
+      r[1][a] = y[3 + a] - S.cB * y[a];
+      r[2][a] = y[3 + a] + S.cA * y[a];
+      vv[0][a] = v1;
+      vv[1][a] = v2 - S.cB * v1;
+      vv[2][a] = v2 + S.cA * v1;
+    }
+    int nb = 0, which = -1;
+    double Ep[3], L2p[3];
+    PairBound pbs[3];
+    for (int k = 0; k < 3; ++k) {
+      const double mu = S.mu_pair[k];
+      const double d = sqrt(r[k][0] * r[k][0] + r[k][1] * r[k][1] + r[k][2] * r[k][2]);
+      const double v2 = vv[k][0] * vv[k][0] + vv[k][1] * vv[k][1] + vv[k][2] * vv[k][2];
+      const double Lx = r[k][1] * vv[k][2] - r[k][2] * vv[k][1];
+      const double Ly = r[k][2] * vv[k][0] - r[k][0] * vv[k][2];
+      const double Lz = r[k][0] * vv[k][1] - r[k][1] * vv[k][0];
+      Ep[k] = 0.5 * mu * v2 + pot_V(S.pair[k], d);
+      L2p[k] = mu * mu * (Lx * Lx + Ly * Ly + Lz * Lz);
+      pbs[k] = pair_bound(S.pair[k], shapes[sid * 3 + k], mu, L2p[k], Ep[k], d);
+      if (pbs[k].bound) { ++nb; which = k; }
+    }
+    if (nb == 0) cls = QCAMS_CLS_D;
+    else if (nb > 1) cls = QCAMS_CLS_AMBIG;
+    else {
+      cls = which == 0 ? QCAMS_CLS_Q : which == 2 ? QCAMS_CLS_R_AC : QCAMS_CLS_R_BC;
+      const DevPair& q = S.pair[which];
+      const DevShape& sh = shapes[sid * 3 + which];
+      const double mu = S.mu_pair[which];
+      double rm, rp, act, per;
+      vp = -0.5;
+      if (turning_points(q, sh, mu, L2p[which], Ep[which], pbs[which].r_min, pbs[which].r_top,
+                         &rm, &rp)) {
+        action_period<kGL64>(q, mu, L2p[which], Ep[which], rm, rp, &act, &per);
+        vp = -0.5 + sqrt(2.0 * mu) / kPi * act;
+      }
+      jp = -0.5 + 0.5 * sqrt(1.0 + 4.0 * L2p[which]);
+      vt = (int)floor(vp + 0.5);
+      if (vt < 0) vt = 0;
+      jt = (int)floor(jp + 0.5);
+      const double dv = vp - vt;
+      w = exp(-dv * dv / (2.0 * gb_sigma * gb_sigma)) / (gb_sigma * sqrt(2.0 * kPi));
+    }
+  }
+  B.cls[i] = (uint8_t)cls;
+  B.vprime[i] = vp;
+  B.jprime[i] = jp;
+  B.gbw[i] = w;
+  B.vt[i] = (int16_t)(vt > 32767 ? 32767 : vt);
+  B.jt[i] = (int16_t)(jt > 32767 ? 32767 : jt);
+  B.dE[i] = dE;
+}
+
+// ---------------------------------------------------------------------------
+// Histogram reduction (Sec. 2.3): each block takes a contiguous chunk of
+// lanes and accumulates the per-cell records of up to kSlots distinct cells
+// in shared memory (64-bit shared atomics); lanes of further cells go to
+// global memory directly.  Fixed-point sums make the result independent of
+// the order of the additions.
+// ---------------------------------------------------------------------------
+constexpr int kSlots = 2;
+constexpr int kReduceBlock = 512;
+constexpr int kReduceChunk = 8192;
+
+__device__ __forceinline__ unsigned long long fixp(double x) {
+  return (unsigned long long)__double2ll_rn(x * 4294967296.0);
+}
+
+__global__ void __launch_bounds__(kReduceBlock) k_reduce(DevBatch B, int n_cells,
+                                                         unsigned long long* hist) {
+  __shared__ int slot_cell[kSlots];
+  __shared__ unsigned long long sh[kSlots][QCAMS_H_STRIDE];
+  const int tid = threadIdx.x;
+  if (tid < kSlots) slot_cell[tid] = -1;
+  for (int k = tid; k < kSlots * QCAMS_H_STRIDE; k += blockDim.x) (&sh[0][0])[k] = 0ull;
+  __syncthreads();
+  const int64_t begin = (int64_t)blockIdx.x * kReduceChunk;
+  const int64_t end = min(B.n, begin + kReduceChunk);
+  for (int64_t i = begin + tid; i < end; i += blockDim.x) {
+    const int c = B.cell[i];
+    if (c < 0 || c >= n_cells) continue;
+    int slot = -1;
+    for (int k = 0; k < kSlots && slot < 0; ++k) {
+      int cur = slot_cell[k];
+      if (cur == c) slot = k;
+      else if (cur == -1) {
+        int prev = atomicCAS(&slot_cell[k], -1, c);
+        if (prev == -1 || prev == c) slot = k;
+      }
+    }
+    unsigned long long* H = slot >= 0 ? sh[slot] : hist + (size_t)c * QCAMS_H_STRIDE;
+    int k = B.cls[i];
+    if (k < 0 || k >= QCAMS_N_CLS) k = QCAMS_CLS_FAIL;
+    const double wv = B.isw ? B.isw[i] : 1.0;
+    atomicAdd(&H[QCAMS_H_COUNT + k], 1ull);
+    atomicAdd(&H[QCAMS_H_COUNT + 6], 1ull);
+    atomicAdd(&H[QCAMS_H_W + k], fixp(wv));
+    atomicAdd(&H[QCAMS_H_W2 + k], fixp(wv * wv));
+    if (k <= 2) {
+      const int v = max(0, min((int)B.vt[i], 63));
+      const int jj = max(0, min((int)B.jt[i], 255));
+      atomicAdd(&H[QCAMS_H_VT + 64 * k + v], 1ull);
+      atomicAdd(&H[QCAMS_H_JT + 256 * k + jj], 1ull);
+      atomicAdd(&H[QCAMS_H_GB + 64 * k + v], fixp(B.gbw[i]));
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < kSlots; ++s) {
+    const int c = slot_cell[s];
+    if (c < 0) continue;
+    unsigned long long* G = hist + (size_t)c * QCAMS_H_STRIDE;
+    for (int k = tid; k < QCAMS_H_STRIDE; k += blockDim.x) {
+      const unsigned long long v = sh[s][k];
+      if (v) atomicAdd(&G[k], v);
+    }
+  }
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? QCAMS_OK : QCAMS_E_CUDA; }
+
+int check_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QCAMS_E_NODEVICE;
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return QCAMS_E_NODEVICE;
+  if (major != 10 || minor != 3) return QCAMS_E_NODEVICE;
+  return QCAMS_OK;
+}
+
+}  // namespace
+}  // namespace qcams
+
+using namespace qcams;
+
+extern "C" {
+
+const char* qcams_status_string(int code) {
+  switch (code) {
+    case QCAMS_OK: return "ok";
+    case QCAMS_E_INVALID: return "invalid argument";
+    case QCAMS_E_NO_LEVEL: return "requested (v, j) level does not exist";
+    case QCAMS_E_CUDA: return "CUDA runtime error";
+    case QCAMS_E_CAPACITY: return "size exceeds a library limit";
+    case QCAMS_E_TIMEOUT: return "bounded device wait gave up";
+    case QCAMS_E_NODEVICE: return "no CUDA device of compute capability 10.3";
+    default: return "unknown status";
+  }
+}
+
+int qcams_system_setup(const double mass_u[3], const int32_t kind[3], const double spec[3][5],
+                       qcams_system* out) {
+  if (!mass_u || !kind || !spec || !out) return QCAMS_E_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  for (int i = 0; i < 3; ++i) {
+    if (!finite_pos(mass_u[i])) return QCAMS_E_INVALID;
+    out->mass[i] = mass_u[i] * kAmu;
+  }
+  static const int pa[3] = {0, 1, 2}, pb[3] = {1, 2, 0};
+  for (int k = 0; k < 3; ++k) {
+    const double* q = spec[k];
+    qcams_pair& P = out->pair[k];
+    const double ma = out->mass[pa[k]], mb = out->mass[pb[k]];
+    const double mu = ma * mb / (ma + mb);
+    switch (kind[k]) {
+      case QCAMS_SPEC_MORSE:
+        P.kind = QCAMS_MORSE; P.p[0] = q[0]; P.p[1] = q[1]; P.p[2] = q[2];
+        break;
+      case QCAMS_SPEC_LJ:
+        P.kind = QCAMS_LJ;
+        for (int i = 0; i < 5; ++i) P.p[i] = q[i];
+        break;
+      case QCAMS_SPEC_BUCK:
+        P.kind = QCAMS_BUCK;
+        for (int i = 0; i < 4; ++i) P.p[i] = q[i];
+        break;
+      case QCAMS_SPEC_LJ_FIT: {
+        // V'(re) = 0 and V(re) = -De for V = Cm r^-m - Cn r^-n
+        const double m = q[0], n = q[1], De = q[2], re = q[3];
+        if (!(m > n) || !finite_pos(De) || !finite_pos(re)) return QCAMS_E_INVALID;
+        P.kind = QCAMS_LJ;
+        P.p[0] = m;
+        P.p[1] = n;
+        P.p[2] = De * n * std::pow(re, m) / (m - n);
+        P.p[3] = De * m * std::pow(re, n) / (m - n);
+        P.p[4] = re;
+        break;
+      }
+      case QCAMS_SPEC_MORSE_WE:
+        if (!finite_pos(q[0])) return QCAMS_E_INVALID;
+        P.kind = QCAMS_MORSE;
+        P.p[0] = q[0];
+        P.p[1] = q[1];
+        P.p[2] = q[2] * std::sqrt(mu / (2.0 * q[0]));
+        break;
+      default:
+        return QCAMS_E_INVALID;
+    }
+    DevPair tmp;
+    int rc = make_devpair(P, &tmp);
+    if (rc != QCAMS_OK) return rc;
+  }
+  return QCAMS_OK;
+}
+
+int qcams_levels(const qcams_system* sys, int32_t n_sys, const int32_t* sys_id, const int32_t* v,
+                 const int32_t* j, int32_t n_levels, qcams_level* out, void* cuda_stream) {
+  SysSet ss;
+  int rc = make_sysset(sys, n_sys, &ss);
+  if (rc != QCAMS_OK) return rc;
+  if (n_levels < 0 || (n_levels > 0 && (!sys_id || !v || !j || !out))) return QCAMS_E_INVALID;
+  if (n_levels > kMaxLevelsReq) return QCAMS_E_CAPACITY;
+  if (n_levels == 0) return QCAMS_OK;
+  std::vector<int32_t> req(3 * (size_t)n_levels);
+  for (int k = 0; k < n_levels; ++k) {
+    if (sys_id[k] < 0 || sys_id[k] >= n_sys || v[k] < 0 || j[k] < 0 || v[k] > 100000 ||
+        j[k] > 100000)
+      return QCAMS_E_INVALID;
+    req[3 * k] = sys_id[k];
+    req[3 * k + 1] = v[k];
+    req[3 * k + 2] = j[k];
+  }
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  Ctx* ctx;
+  if (ctx_get(&ctx) != cudaSuccess) return QCAMS_E_CUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemcpyAsync(ctx->req_in, req.data(), req.size() * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  k_pair_shapes<<<1, 32, 0, st>>>(ss, ctx->shapes);
+  k_levels_list<<<(n_levels + 63) / 64, 64, 0, st>>>(ss, ctx->shapes, ctx->req_in, n_levels,
+                                                      ctx->req_out);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, ctx->req_out, sizeof(qcams_level) * n_levels, cudaMemcpyDeviceToHost,
+                        st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  for (int k = 0; k < n_levels; ++k)
+    if (!out[k].ok) return QCAMS_E_NO_LEVEL;
+  return QCAMS_OK;
+}
+
+int qcams_init_states(const qcams_system* sys, int32_t n_sys, const double* E_col, const double* b,
+                      const int32_t* v, const int32_t* j, double R0, uint64_t seed,
+                      uint64_t id_offset, const double* const* u_in, qcams_batch* batch,
+                      void* cuda_stream) {
+  SysSet ss;
+  int rc = make_sysset(sys, n_sys, &ss);
+  if (rc != QCAMS_OK) return rc;
+  if ((rc = check_batch(batch, false)) != QCAMS_OK) return rc;
+  if (!finite_pos(R0)) return QCAMS_E_INVALID;
+  if (batch->n == 0) return QCAMS_OK;
+  if (!E_col || !b || !v || !j) return QCAMS_E_INVALID;
+  if (u_in && (!u_in[0] || !u_in[1] || !u_in[2] || !u_in[3])) return QCAMS_E_INVALID;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  Ctx* ctx;
+  if (ctx_get(&ctx) != cudaSuccess) return QCAMS_E_CUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  DevBatch d = dev_batch(batch);
+  const int64_t n = batch->n;
+  const unsigned grid = (unsigned)((n + 255) / 256);
+  k_pair_shapes<<<1, 32, 0, st>>>(ss, ctx->shapes);
+  cudaError_t e = cudaMemsetAsync(ctx->level_flag, 0, kLevelCells, st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  k_mark_levels<<<grid, 256, 0, st>>>(n, batch->sys_id, v, j, n_sys, ctx->level_flag);
+  k_solve_levels<<<(kLevelCells + 63) / 64, 64, 0, st>>>(ss, ctx->shapes, ctx->level_flag,
+                                                          ctx->levels);
+  k_init<<<grid, 256, 0, st>>>(ss, ctx->levels, E_col, b, v, j, R0, seed, id_offset,
+                               u_in ? u_in[0] : nullptr, u_in ? u_in[1] : nullptr,
+                               u_in ? u_in[2] : nullptr, u_in ? u_in[3] : nullptr, d);
+  return cuda_status(cudaGetLastError());
+}
+
+int qcams_run_batch(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
+                    qcams_batch* batch, void* cuda_stream) {
+  SysSet ss;
+  int rc = make_sysset(sys, n_sys, &ss);
+  if (rc != QCAMS_OK) return rc;
+  IntegParams ip;
+  if ((rc = make_integ_params(integ, &ip)) != QCAMS_OK) return rc;
+  if ((rc = check_batch(batch, !integ->fixed_step)) != QCAMS_OK) return rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  Ctx* ctx;
+  if (ctx_get(&ctx) != cudaSuccess) return QCAMS_E_CUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (batch->n == 0) return QCAMS_OK;
+  DevBatch d = dev_batch(batch);
+  k_pair_shapes<<<1, 32, 0, st>>>(ss, ctx->shapes);
+  ctx->timed = false;
+  cudaError_t e = cudaEventRecord(ctx->ev[0], st);
+  if (e == cudaSuccess)
+    e = launch_integrate(ss, ctx->shapes, ip, d, integ->precision, integ->persistent,
+                         integ->block, integ->blocks_per_sm, *ctx, st);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  if (integ->fixed_step) {
+    e = cudaEventRecord(ctx->ev[2], st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], st);
+    ctx->timed = e == cudaSuccess;
+    return cuda_status(e);
+  }
+  const double sg = integ->gb_sigma > 0 ? integ->gb_sigma : 0.1 / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+  e = cudaEventRecord(ctx->ev[2], st);
+  k_analyze<<<(unsigned)((batch->n + 127) / 128), 128, 0, st>>>(ss, ctx->shapes, sg, d);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], st);
+  ctx->timed = e == cudaSuccess;
+  return cuda_status(e);
+}
+
+int qcams_analyze(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
+                  qcams_batch* batch, void* cuda_stream) {
+  SysSet ss;
+  int rc = make_sysset(sys, n_sys, &ss);
+  if (rc != QCAMS_OK) return rc;
+  if (!integ) return QCAMS_E_INVALID;
+  if ((rc = check_batch(batch, true)) != QCAMS_OK) return rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  Ctx* ctx;
+  if (ctx_get(&ctx) != cudaSuccess) return QCAMS_E_CUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (batch->n == 0) return QCAMS_OK;
+  DevBatch d = dev_batch(batch);
+  k_pair_shapes<<<1, 32, 0, st>>>(ss, ctx->shapes);
+  const double sg = integ->gb_sigma > 0 ? integ->gb_sigma : 0.1 / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+  k_analyze<<<(unsigned)((batch->n + 127) / 128), 128, 0, st>>>(ss, ctx->shapes, sg, d);
+  return cuda_status(cudaGetLastError());
+}
+
+int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_t* hist_out,
+                      double* xsec_out, void* cuda_stream) {
+  if (!batch || !cells || !hist_out || batch->n < 0) return QCAMS_E_INVALID;
+  if (cells->n_cells < 1 || cells->n_groups < 0) return QCAMS_E_INVALID;
+  if (cells->n_cells > kMaxCells || cells->n_groups > kMaxCells) return QCAMS_E_CAPACITY;
+  if (batch->n > 0 && (!batch->cell || !batch->cls || !batch->vt || !batch->jt || !batch->gbw))
+    return QCAMS_E_INVALID;
+  if (cells->weighted && !batch->isw) return QCAMS_E_INVALID;
+  if (xsec_out && (!cells->b || !cells->w || (cells->n_groups > 0 && !cells->group)))
+    return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t nh = (size_t)cells->n_cells * QCAMS_H_STRIDE;
+  cudaError_t e = cudaMemsetAsync(hist_out, 0, nh * sizeof(int64_t), st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  if (batch->n > 0) {
+    DevBatch d = dev_batch(batch);
+    const unsigned grid = (unsigned)((batch->n + kReduceChunk - 1) / kReduceChunk);
+    k_reduce<<<grid, kReduceBlock, 0, st>>>(d, cells->n_cells, (unsigned long long*)hist_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return QCAMS_E_CUDA;
+  }
+  if (!xsec_out) return QCAMS_OK;
+  std::vector<int64_t> H(nh);
+  e = cudaMemcpyAsync(H.data(), hist_out, nh * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  // Opacity and binomial error per cell (Eqs. 13, 16); cross sections per
+  // group as 2 pi sum w b P (Eq. 18 with the angular measure divided out).
+  const int nc = cells->n_cells, ng = cells->n_groups;
+  std::vector<double> var(6 * (size_t)(ng > 0 ? ng : 1), 0.0);
+  double* grp = xsec_out + 12 * (size_t)nc;
+  for (size_t k = 0; k < 12 * (size_t)ng; ++k) grp[k] = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const int64_t* h = H.data() + (size_t)c * QCAMS_H_STRIDE;
+    double N = 0.0;
+    for (int k = 0; k < 5; ++k) N += (double)h[QCAMS_H_COUNT + k];
+    for (int k = 0; k < 6; ++k) {
+      double P = 0.0, dl = 0.0;
+      if (N > 0) {
+        if (!cells->weighted) {
+          const double Nx = (double)h[QCAMS_H_COUNT + k];
+          P = Nx / N;
+          dl = std::sqrt(Nx) / N * std::sqrt((N - Nx) / N);
+        } else {
+          const double sw = std::ldexp((double)h[QCAMS_H_W + k], -32);
+          const double sw2 = std::ldexp((double)h[QCAMS_H_W2 + k], -32);
+          P = sw / N;
+          dl = N > 1 ? std::sqrt(std::fmax(0.0, sw2 / N - P * P) / (N - 1.0)) : 0.0;
+        }
+      }
+      xsec_out[12 * (size_t)c + 2 * k] = P;
+      xsec_out[12 * (size_t)c + 2 * k + 1] = dl;
+      const int g = ng > 0 ? cells->group[c] : -1;
+      if (g >= 0 && g < ng) {
+        const double wb = cells->w[c] * cells->b[c];
+        grp[12 * (size_t)g + 2 * k] += 2.0 * kPi * wb * P;
+        var[6 * (size_t)g + k] += (wb * dl) * (wb * dl);
+      }
+    }
+  }
+  for (int g = 0; g < ng; ++g)
+    for (int k = 0; k < 6; ++k)
+      grp[12 * (size_t)g + 2 * k + 1] = 2.0 * kPi * std::sqrt(var[6 * (size_t)g + k]);
+  return QCAMS_OK;
+}
+
+int qcams_last_run_stats(qcams_run_stats* out, void* cuda_stream) {
+  if (!out) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  Ctx* ctx;
+  if (ctx_get(&ctx) != cudaSuccess) return QCAMS_E_CUDA;
+  unsigned long long h[2];
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMemcpyAsync(h, ctx->counters, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  out->rhs = (int64_t)h[0];
+  out->steps = (int64_t)h[1];
+  out->integrate_ms = 0.0;
+  out->analyze_ms = 0.0;
+  if (ctx->timed) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess) out->integrate_ms = a;
+    if (cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]) == cudaSuccess) out->analyze_ms = b;
+  }
+  return QCAMS_OK;
+}
+
+int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor) {
+  if (!sm_count || !cc_major || !cc_minor) return QCAMS_E_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QCAMS_E_NODEVICE;
+  int a = 0, b = 0, c = 0;
+  if (cudaDeviceGetAttribute(&a, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return QCAMS_E_NODEVICE;
+  *sm_count = a;
+  *cc_major = b;
+  *cc_minor = c;
+  return QCAMS_OK;
+}
+
+int qcams_shutdown(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QCAMS_E_NODEVICE;
+  if (dev < 0 || dev >= kMaxDevices) return QCAMS_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  Ctx* c = g_ctx[dev];
+  if (!c) return QCAMS_OK;
+  cudaDeviceSynchronize();
+  cudaFree(c->shapes); cudaFree(c->levels); cudaFree(c->level_flag); cudaFree(c->counters);
+  cudaFree(c->req_out); cudaFree(c->req_in);
+  for (int k = 0; k < 4; ++k) if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+  delete c;
+  g_ctx[dev] = nullptr;
+  return QCAMS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// Internal host-side interface between the C-ABI layer (api.cu) and the
+// kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qcams_device.cuh"
+
+namespace qcams {
+
+// Library-owned per-device scratch (created lazily, freed by qcams_shutdown).
+struct Ctx {
+  int device = -1;
+  int sm_count = 0;
+  DevShape* shapes = nullptr;          // [QCAMS_MAX_SYS][3]
+  DevLevel* levels = nullptr;          // [kLevelCells]
+  uint8_t* level_flag = nullptr;       // [kLevelCells]
+  unsigned long long* counters = nullptr;  // [8]: 0 rhs, 1 steps, 2 queue head
+  qcams_level* req_out = nullptr;      // [65536] qcams_levels output staging
+  int32_t* req_in = nullptr;           // [3 * 65536] qcams_levels input staging
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // integrate / analyze timing
+  bool timed = false;                  // ev[] hold a completed qcams_run_batch
+};
+
+struct IntegParams {
+  double rtol, atol, r_stop2, t_stop, h_fixed;
+  long long max_steps;
+  int fixed_step;
+};
+
+// Launch the integrator over the batch (integrate.cu).
+cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
+                             const DevBatch& b, int precision, int persistent, int block,
+                             int blocks_per_sm, Ctx& ctx, cudaStream_t st);
+
+}  // namespace qcams

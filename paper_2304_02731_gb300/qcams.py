@@ -1,0 +1,387 @@
+"""Python binding of the QCT C ABI (include/qcams.h).
+
+Argument marshalling only: every step of the trajectory path runs in the
+CUDA kernels of libqcams.so.  PyTorch provides device memory and streams.
+The binding fails loudly if the library cannot be loaded; there is no CPU
+fallback.
+
+Function names follow the C ABI: ``init_states``, ``run_batch``,
+``analyze``, ``reduce_xsec``, ``levels``; ``Batch`` owns the structure-of-
+arrays device tensors of one batch of trajectories.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "_build", "libqcams.so")
+_lock = threading.Lock()
+_lib = None
+
+# status / class codes and histogram layout (include/qcams.h)
+LANE = dict(READY=0, RUNNING=1, DONE_RSTOP=2, DONE_TMAX=3, FAIL_MAXSTEPS=4, FAIL_HMIN=5,
+            FAIL_NAN=6, FAIL_COLLAPSE=7, NO_LEVEL=8, INVALID=9)
+CLS = dict(Q=0, R_AC=1, R_BC=2, D=3, AMBIG=4, FAIL=5)
+H_COUNT, H_VT, H_JT, H_GB, H_W, H_W2, H_STRIDE = 0, 8, 200, 968, 1160, 1168, 1176
+SPEC_KIND = dict(morse=0, lj=1, buck=2, lj_fit=3, morse_we=4)
+GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+
+EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
+           "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
+           "qcams_fma_peak", "qcams_device_info", "qcams_shutdown"]
+
+
+class QcamsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = lib().qcams_status_string(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+class Pair(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("p", C.c_double * 5)]
+
+
+class System(C.Structure):
+    _fields_ = [("mass", C.c_double * 3), ("pair", Pair * 3)]
+
+
+class Integ(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("r_stop", C.c_double),
+                ("t_stop", C.c_double), ("h_fixed", C.c_double), ("gb_sigma", C.c_double),
+                ("max_steps", C.c_int64), ("fixed_step", C.c_int32), ("precision", C.c_int32),
+                ("persistent", C.c_int32), ("block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+class Level(C.Structure):
+    _fields_ = [("E", C.c_double), ("r_minus", C.c_double), ("r_plus", C.c_double),
+                ("tau", C.c_double), ("ok", C.c_int32), ("pad", C.c_int32)]
+
+
+class CBatch(C.Structure):
+    _fields_ = [("n", C.c_int64), ("sys_id", C.c_void_p), ("cell", C.c_void_p),
+                ("isw", C.c_void_p), ("y", C.c_void_p * 12), ("t", C.c_void_p),
+                ("h", C.c_void_p), ("t_scale", C.c_void_p), ("E0", C.c_void_p),
+                ("Ecol", C.c_void_p), ("u", C.c_void_p * 4), ("status", C.c_void_p),
+                ("cls", C.c_void_p), ("nsteps", C.c_void_p), ("nrej", C.c_void_p),
+                ("dE", C.c_void_p), ("vprime", C.c_void_p), ("jprime", C.c_void_p),
+                ("gbw", C.c_void_p), ("vt", C.c_void_p), ("jt", C.c_void_p)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("rhs", C.c_int64), ("steps", C.c_int64), ("integrate_ms", C.c_double),
+                ("analyze_ms", C.c_double)]
+
+
+class Cells(C.Structure):
+    _fields_ = [("n_cells", C.c_int32), ("n_groups", C.c_int32), ("b", C.c_void_p),
+                ("w", C.c_void_p), ("group", C.c_void_p), ("weighted", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libqcams.so (built by paper_2304_02731_gb300.build); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise RuntimeError(
+                    f"QCT CUDA library not built ({_LIB_PATH}); run "
+                    "`python -c 'import __graft_entry__ as g; g.build()'` first")
+            L = C.CDLL(_LIB_PATH)
+            P, V, I32, I64, D = C.POINTER, C.c_void_p, C.c_int32, C.c_int64, C.c_double
+            sig = {
+                "qcams_status_string": (C.c_char_p, [C.c_int]),
+                "qcams_system_setup": (C.c_int, [P(D), P(I32), P(D), P(System)]),
+                "qcams_levels": (C.c_int, [P(System), I32, P(I32), P(I32), P(I32), I32, P(Level),
+                                           V]),
+                "qcams_init_states": (C.c_int, [P(System), I32, V, V, V, V, D, C.c_uint64,
+                                                C.c_uint64, V, P(CBatch), V]),
+                "qcams_run_batch": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
+                "qcams_analyze": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
+                "qcams_reduce_xsec": (C.c_int, [P(CBatch), P(Cells), V, V, V]),
+                "qcams_last_run_stats": (C.c_int, [P(RunStats), V]),
+                "qcams_fma_peak": (C.c_int, [I32, P(D), V]),
+                "qcams_device_info": (C.c_int, [P(I32), P(I32), P(I32)]),
+                "qcams_shutdown": (C.c_int, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise QcamsError(code, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# systems and parameters
+# ---------------------------------------------------------------------------
+def system_setup(spec) -> System:
+    """spec: dict(mass_u=(mA, mB, mC), pairs=[(kind_name, *params)] * 3)."""
+    mass = (C.c_double * 3)(*[float(x) for x in spec["mass_u"]])
+    kinds = (C.c_int32 * 3)()
+    par = (C.c_double * 15)()
+    for k, pr in enumerate(spec["pairs"]):
+        kinds[k] = SPEC_KIND[pr[0]]
+        for i, x in enumerate(pr[1:]):
+            par[5 * k + i] = float(x)
+    out = System()
+    _check(lib().qcams_system_setup(mass, kinds, par, C.byref(out)), "qcams_system_setup")
+    return out
+
+
+def systems_array(systems):
+    arr = (System * len(systems))()
+    for i, s in enumerate(systems):
+        arr[i] = s if isinstance(s, System) else system_setup(s)
+    return arr
+
+
+def make_integ(rtol=1e-10, atol=1e-12, r_stop=35.0, t_stop=15.0, h_fixed=0.0,
+               gb_sigma=GB_SIGMA_DEFAULT, max_steps=1_000_000, fixed_step=False, precision=64,
+               persistent=False, block=0, blocks_per_sm=0) -> Integ:
+    return Integ(rtol, atol, r_stop, t_stop, h_fixed, gb_sigma, int(max_steps),
+                 int(bool(fixed_step)), int(precision), int(bool(persistent)), int(block),
+                 int(blocks_per_sm), 0)
+
+
+# ---------------------------------------------------------------------------
+# batches
+# ---------------------------------------------------------------------------
+_FIELDS_F64 = ["t", "h", "t_scale", "E0", "Ecol", "dE", "vprime", "jprime", "gbw"]
+
+
+@dataclass
+class Batch:
+    """Structure-of-arrays device storage for n trajectories (qcams_batch)."""
+    n: int
+    device: torch.device
+    y: torch.Tensor          # [12, n] float64
+    f64: dict                # name -> [n] float64
+    sys_id: torch.Tensor
+    cell: torch.Tensor
+    isw: torch.Tensor | None
+    u: torch.Tensor | None   # [4, n] float64 (uniforms written by init)
+    status: torch.Tensor
+    cls: torch.Tensor
+    nsteps: torch.Tensor
+    nrej: torch.Tensor
+    vt: torch.Tensor
+    jt: torch.Tensor
+    _c: CBatch = None
+
+    @staticmethod
+    def empty(n: int, device="cuda", sys_id=None, cell=None, isw=None, keep_u=True) -> "Batch":
+        dev = torch.device(device)
+        z = lambda dt: torch.zeros(n, dtype=dt, device=dev)
+        sid = z(torch.int32) if sys_id is None else torch.as_tensor(
+            sys_id, dtype=torch.int32).to(dev).contiguous()
+        cel = z(torch.int32) if cell is None else torch.as_tensor(
+            cell, dtype=torch.int32).to(dev).contiguous()
+        w = None if isw is None else torch.as_tensor(isw, dtype=torch.float64).to(dev).contiguous()
+        b = Batch(n=n, device=dev, y=torch.zeros(12, n, dtype=torch.float64, device=dev),
+                  f64={k: z(torch.float64) for k in _FIELDS_F64}, sys_id=sid, cell=cel, isw=w,
+                  u=torch.zeros(4, n, dtype=torch.float64, device=dev) if keep_u else None,
+                  status=z(torch.uint8), cls=z(torch.uint8), nsteps=z(torch.int32),
+                  nrej=z(torch.int32), vt=z(torch.int16), jt=z(torch.int16))
+        b._build()
+        return b
+
+    def _build(self):
+        c = CBatch()
+        c.n = self.n
+        c.sys_id = self.sys_id.data_ptr()
+        c.cell = self.cell.data_ptr()
+        c.isw = self.isw.data_ptr() if self.isw is not None else None
+        for k in range(12):
+            c.y[k] = self.y[k].data_ptr()
+        for name in _FIELDS_F64:
+            setattr(c, name, self.f64[name].data_ptr())
+        for k in range(4):
+            c.u[k] = self.u[k].data_ptr() if self.u is not None else None
+        c.status = self.status.data_ptr()
+        c.cls = self.cls.data_ptr()
+        c.nsteps = self.nsteps.data_ptr()
+        c.nrej = self.nrej.data_ptr()
+        c.vt = self.vt.data_ptr()
+        c.jt = self.jt.data_ptr()
+        self._c = c
+
+    @property
+    def c(self) -> CBatch:
+        return self._c
+
+    def state(self) -> np.ndarray:
+        """[n, 12] host copy of the phase-space state."""
+        return self.y.t().contiguous().cpu().numpy()
+
+    def set_state(self, y: np.ndarray):
+        self.y.copy_(torch.as_tensor(np.ascontiguousarray(y.T), dtype=torch.float64))
+
+    def host(self) -> dict:
+        out = {k: v.cpu().numpy() for k, v in self.f64.items()}
+        for k in ["status", "cls", "nsteps", "nrej", "vt", "jt"]:
+            out[k] = getattr(self, k).cpu().numpy()
+        out["y"] = self.state()
+        if self.u is not None:
+            out["u"] = self.u.t().contiguous().cpu().numpy()
+        return out
+
+
+def _dptr(x, dtype, device):
+    t = torch.as_tensor(x, dtype=dtype)
+    if t.device != device:
+        t = t.to(device, non_blocking=True)
+    return t.contiguous()
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+def levels(systems, sys_id, v, j, stream=None):
+    """qcams_levels: Bohr-Sommerfeld levels (host in / host out)."""
+    arr = systems_array(systems)
+    n = len(v)
+    sid = np.ascontiguousarray(sys_id, np.int32)
+    vv = np.ascontiguousarray(v, np.int32)
+    jj = np.ascontiguousarray(j, np.int32)
+    out = (Level * n)()
+    P = C.POINTER(C.c_int32)
+    rc = lib().qcams_levels(arr, len(systems), sid.ctypes.data_as(P), vv.ctypes.data_as(P),
+                            jj.ctypes.data_as(P), n, out, _stream(stream))
+    if rc not in (0, -2):
+        _check(rc, "qcams_levels")
+    return np.array([(L.E, L.r_minus, L.r_plus, L.tau, L.ok) for L in out],
+                    dtype=[("E", "f8"), ("r_minus", "f8"), ("r_plus", "f8"), ("tau", "f8"),
+                           ("ok", "i4")])
+
+
+def init_states(systems, batch: Batch, E, b, v, j, R0: float, seed: int, id_offset: int = 0,
+                u_in=None, stream=None):
+    """qcams_init_states on `batch` (inputs may be host or device arrays)."""
+    arr = systems_array(systems)
+    dev = batch.device
+    tE = _dptr(E, torch.float64, dev)
+    tb = _dptr(b, torch.float64, dev)
+    tv = _dptr(v, torch.int32, dev)
+    tj = _dptr(j, torch.int32, dev)
+    keep = [tE, tb, tv, tj]
+    uptr = None
+    if u_in is not None:
+        tu = _dptr(u_in, torch.float64, dev).reshape(4, batch.n)
+        keep.append(tu)
+        uptr = (C.c_void_p * 4)(*[tu[k].data_ptr() for k in range(4)])
+    rc = lib().qcams_init_states(arr, len(systems), tE.data_ptr(), tb.data_ptr(), tv.data_ptr(),
+                                 tj.data_ptr(), float(R0), int(seed), int(id_offset), uptr,
+                                 C.byref(batch.c), _stream(stream))
+    _check(rc, "qcams_init_states")
+    # the staged inputs are consumed asynchronously on `stream`
+    s = stream if stream is not None else torch.cuda.current_stream()
+    for t in keep:
+        t.record_stream(s)
+    return keep
+
+
+def run_batch(systems, batch: Batch, integ: Integ, stream=None):
+    """qcams_run_batch: integrate (and, unless fixed-step, analyse) the batch."""
+    arr = systems_array(systems)
+    _check(lib().qcams_run_batch(arr, len(systems), C.byref(integ), C.byref(batch.c),
+                                 _stream(stream)), "qcams_run_batch")
+
+
+def analyze(systems, batch: Batch, integ: Integ, stream=None):
+    arr = systems_array(systems)
+    _check(lib().qcams_analyze(arr, len(systems), C.byref(integ), C.byref(batch.c),
+                               _stream(stream)), "qcams_analyze")
+
+
+def reduce_xsec(batch: Batch, n_cells: int, cell_b=None, cell_w=None, group=None, n_groups=0,
+                weighted=False, hist_out: torch.Tensor | None = None, stream=None,
+                finalize=True):
+    """qcams_reduce_xsec.  Returns (hist [n_cells, H_STRIDE] device tensor,
+    cells [n_cells, 6, 2] and groups [n_groups, 6, 2] host arrays or None)."""
+    if hist_out is None:
+        hist_out = torch.empty(n_cells * H_STRIDE, dtype=torch.int64, device=batch.device)
+    cells = Cells()
+    cells.n_cells = int(n_cells)
+    cells.n_groups = int(n_groups)
+    keep = []
+    if finalize:
+        cb = np.ascontiguousarray(cell_b, np.float64)
+        cw = np.ascontiguousarray(cell_w, np.float64)
+        cg = np.ascontiguousarray(group if group is not None else np.zeros(n_cells), np.int32)
+        keep += [cb, cw, cg]
+        cells.b = cb.ctypes.data
+        cells.w = cw.ctypes.data
+        cells.group = cg.ctypes.data
+    cells.weighted = int(bool(weighted))
+    out = np.zeros(12 * n_cells + 12 * n_groups) if finalize else None
+    rc = lib().qcams_reduce_xsec(C.byref(batch.c), C.byref(cells), C.c_void_p(hist_out.data_ptr()),
+                                 C.c_void_p(out.ctypes.data) if finalize else None,
+                                 _stream(stream))
+    _check(rc, "qcams_reduce_xsec")
+    hist = hist_out.view(n_cells, H_STRIDE)
+    if not finalize:
+        return hist, None, None
+    return (hist, out[:12 * n_cells].reshape(n_cells, 6, 2),
+            out[12 * n_cells:].reshape(n_groups, 6, 2))
+
+
+def last_run_stats(stream=None) -> dict:
+    """qcams_last_run_stats: work counters and kernel times of the last run."""
+    st = RunStats()
+    _check(lib().qcams_last_run_stats(C.byref(st), _stream(stream)), "qcams_last_run_stats")
+    return dict(rhs=st.rhs, steps=st.steps, integrate_ms=st.integrate_ms,
+                analyze_ms=st.analyze_ms)
+
+
+def fma_peak(precision: int = 64, stream=None) -> float:
+    f = C.c_double()
+    _check(lib().qcams_fma_peak(int(precision), C.byref(f), _stream(stream)), "qcams_fma_peak")
+    return f.value
+
+
+def device_info():
+    a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().qcams_device_info(C.byref(a), C.byref(b), C.byref(c)), "qcams_device_info")
+    return a.value, (b.value, c.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience: a whole workload in one call
+# ---------------------------------------------------------------------------
+def run_workload(wl, integ: Integ | None = None, device="cuda", stream=None, finalize=True,
+                 batch: Batch | None = None):
+    """init -> run -> reduce for a workloads.Workload; returns (batch, hist, cells, groups)."""
+    if integ is None:
+        integ = make_integ(**wl.integ)
+    if batch is None:
+        batch = Batch.empty(wl.n, device, sys_id=wl.sys_id, cell=wl.cell)
+    init_states(wl.systems, batch, wl.E, wl.b, wl.v, wl.j, wl.R0, wl.seed, wl.id_offset,
+                stream=stream)
+    run_batch(wl.systems, batch, integ, stream=stream)
+    hist, cells, groups = reduce_xsec(batch, wl.n_cells, wl.cell_b, wl.cell_w, wl.cell_group,
+                                      wl.n_groups, stream=stream, finalize=finalize)
+    return batch, hist, cells, groups

@@ -1,0 +1,105 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every function include/qcams.h declares, rejects bad arguments
+before touching a device, and its host-side system set-up agrees with the
+oracle's."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def Q():
+    from paper_2304_02731_gb300 import build
+    build.build()
+    from paper_2304_02731_gb300 import qcams
+    qcams.lib()
+    return qcams
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "qcams.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qcams_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(Q):
+    names = _declared_functions()
+    assert "qcams_init_states" in names and "qcams_run_batch" in names
+    assert "qcams_reduce_xsec" in names
+    L = C.CDLL(Q.library_path())
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(Q.EXPORTS)
+
+
+def test_status_strings(Q):
+    for code in [0, -1, -2, -3, -4, -5, -6, 17]:
+        assert len(Q.lib().qcams_status_string(code)) > 0
+
+
+def test_system_setup_matches_oracle(Q, oracle):
+    from paper_2304_02731_gb300 import workloads as W
+    for spec in [W.SYS_H2_CA_MORSE, W.SYS_H2_CA_BUCK, W.SYS_H2_CA_LJ12, W.SYS_H2_CA_LJ8]:
+        a = Q.system_setup(spec)
+        b = oracle.system_from_spec(spec)
+        for i in range(3):
+            assert a.mass[i] == pytest.approx(b.m[i], rel=1e-15)
+        for k in range(3):
+            assert a.pair[k].kind == b.pair[k].kind
+            for i in range(5):
+                assert a.pair[k].p[i] == pytest.approx(b.pair[k].p[i], rel=1e-14, abs=0)
+    spec = dict(mass_u=(1.0, 1.0, 40.0),
+                pairs=(("morse_we", 0.1645, 1.401, 0.02005), W.CAH_MORSE, W.CAH_MORSE))
+    a, b = Q.system_setup(spec), oracle.system_from_spec(spec)
+    assert a.pair[0].p[2] == pytest.approx(b.pair[0].p[2], rel=1e-15)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(mass_u=(0.0, 1.0, 40.0), pairs=(("morse", 0.17, 1.4, 1.0),) * 3),
+    dict(mass_u=(1.0, 1.0, 40.0), pairs=(("morse", -0.17, 1.4, 1.0),) * 3),
+    dict(mass_u=(1.0, 1.0, 40.0), pairs=(("lj_fit", 6, 12, 0.06, 3.8),) * 3),
+    dict(mass_u=(1.0, 1.0, 40.0), pairs=(("lj", 12.5, 6, 1.0, 1.0, 3.0),) * 3),
+    dict(mass_u=(1.0, 1.0, 40.0), pairs=(("lj", 12, 2, 1.0, 1.0, 3.0),) * 3),
+    dict(mass_u=(1.0, float("nan"), 40.0), pairs=(("morse", 0.17, 1.4, 1.0),) * 3),
+])
+def test_system_setup_rejects_bad_parameters(Q, bad):
+    with pytest.raises(Q.QcamsError) as e:
+        Q.system_setup(bad)
+    assert e.value.code == -1
+
+
+def test_entry_points_reject_bad_arguments_without_a_device(Q):
+    L = Q.lib()
+    from paper_2304_02731_gb300 import workloads as W
+    sysarr = Q.systems_array([W.SYS_H2_CA_MORSE])
+    integ = Q.make_integ()
+    b = Q.CBatch()
+    b.n = 10                      # all pointers NULL
+    assert L.qcams_run_batch(sysarr, 1, C.byref(integ), C.byref(b), None) == -1
+    assert L.qcams_run_batch(sysarr, 0, C.byref(integ), C.byref(b), None) == -1
+    assert L.qcams_run_batch(sysarr, 5, C.byref(integ), C.byref(b), None) == -1
+    assert L.qcams_run_batch(sysarr, 1, None, C.byref(b), None) == -1
+    bad = Q.make_integ(rtol=-1.0)
+    assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
+    bad = Q.make_integ(max_steps=0)
+    assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
+    bad = Q.make_integ(precision=16)
+    assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
+    assert L.qcams_init_states(sysarr, 1, None, None, None, None, 30.0, 0, 0, None,
+                               C.byref(b), None) == -1
+    b.n = -1
+    assert L.qcams_analyze(sysarr, 1, C.byref(integ), C.byref(b), None) == -1
+    cells = Q.Cells()
+    cells.n_cells = 0
+    assert L.qcams_reduce_xsec(C.byref(b), C.byref(cells), None, None, None) == -1
+    cells.n_cells = 1 << 20
+    b.n = 0
+    assert L.qcams_reduce_xsec(C.byref(b), C.byref(cells), C.c_void_p(8), None, None) == -4
+    assert L.qcams_last_run_stats(None, None) == -1
+    f = C.c_double()
+    assert L.qcams_fma_peak(16, C.byref(f), None) == -1

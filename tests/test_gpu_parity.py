@@ -1,0 +1,270 @@
+"""GPU <-> oracle parity through the C ABI (needs a GB300).
+
+Tolerances (stated per test) follow the accuracy targets of the method:
+fixed-step states within 1e-9 relative after 2,000 steps; adaptive runs with
+identical outcome class for >= 99% of lanes and cross sections within 3
+binomial standard errors; integer histograms bit-exact from identical
+per-lane outcomes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2304_02731_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_02731_gb300 import build
+    build.build()
+    from paper_2304_02731_gb300 import qcams
+    qcams.lib()
+    return qcams
+
+
+def _osys(oracle, specs):
+    return [oracle.system_from_spec(s) for s in specs]
+
+
+def _init_both(Q, oracle, specs, E, b, v, j, sys_id, R0=30.0, seed=7, id_offset=0):
+    import torch
+    n = len(E)
+    batch = Q.Batch.empty(n, "cuda", sys_id=sys_id)
+    Q.init_states(specs, batch, E, b, v, j, R0, seed, id_offset)
+    torch.cuda.synchronize()
+    g = batch.host()
+    o = oracle.init(_osys(oracle, specs), sys_id, E, b, v, j, R0, seed, id_offset)
+    return batch, g, o
+
+
+# ---------------------------------------------------------------------------
+def test_fma_peaks(Q):
+    f64 = Q.fma_peak(64)
+    f32 = Q.fma_peak(32)
+    print(f"\nFP64 FMA peak {f64 / 1e12:.3f} TFLOP/s, FP32 {f32 / 1e12:.2f} TFLOP/s")
+    assert f64 > 1e11 and f32 > f64
+
+
+@pytest.mark.parametrize("spec_name,pair,cases", [
+    ("morse", 0, [(v, j) for v in (0, 1, 4, 9, 16) for j in (0, 1, 7, 20)]),
+])
+def test_levels_match_oracle(Q, oracle, spec_name, pair, cases):
+    spec = W.SYS_H2_CA_MORSE
+    s = oracle.system_from_spec(spec)
+    mu = oracle.reduced_masses(s)["mu12"]
+    v = [c[0] for c in cases]
+    j = [c[1] for c in cases]
+    got = Q.levels([spec], np.zeros(len(v), np.int32), v, j)
+    for k, (vv, jj) in enumerate(cases):
+        L = oracle.level(s.pair[0], mu, vv, jj)
+        assert got["ok"][k] == L.ok, (vv, jj)
+        if not L.ok:
+            continue
+        assert abs(got["E"][k] - L.E) <= 1e-12 * abs(L.E) + 1e-15, (vv, jj, got["E"][k], L.E)
+        assert abs(got["r_plus"][k] - L.r_plus) <= 1e-11 * L.r_plus, (vv, jj)
+        assert abs(got["r_minus"][k] - L.r_minus) <= 1e-11 * L.r_minus, (vv, jj)
+        assert abs(got["tau"][k] - L.tau) <= 1e-9 * L.tau, (vv, jj, got["tau"][k], L.tau)
+
+
+def test_level_table_mixed_systems(Q, oracle):
+    """All (v <= 10, j <= 20) H2 levels of the mixed study: 230 exist."""
+    vs, js = np.meshgrid(np.arange(11), np.arange(21), indexing="ij")
+    got = Q.levels([W.SYS_H2_CA_MORSE], np.zeros(231, np.int32), vs.ravel(), js.ravel())
+    assert got["ok"].sum() == 230 and not got["ok"][-1]
+
+
+def test_init_matches_oracle(Q, oracle):
+    E, b, v, j, sid = W.random_states(300, seed=4, sys_count=3, b_max=8.0)
+    specs = [W.SYS_H2_CA_BUCK, W.SYS_H2_CA_LJ12, W.SYS_H2_CA_LJ8]
+    v[0], j[0] = 10, 20          # the one missing level
+    batch, g, o = _init_both(Q, oracle, specs, E, b, v, j, sid, seed=123, id_offset=10 ** 12)
+    assert np.array_equal(g["status"], o["status"])
+    assert g["status"][0] == Q.LANE["NO_LEVEL"]
+    ok = g["status"] == 0
+    assert ok.sum() >= 295
+    # uniforms: the same Philox words
+    assert np.array_equal(g["u"][ok], o["u"][ok])
+    y, yo = g["y"][ok], o["y"][ok]
+    assert np.max(np.abs(y - yo) / (np.abs(yo) + 1.0)) < 1e-11
+    assert np.max(np.abs(g["E0"][ok] - o["E0"][ok])) < 1e-13
+    # t_scale = R / v_rel carries the period tau through R = R0 + chi P2 tau / mu123;
+    # the two sides' period quadratures agree to ~1e-9 relative near dissociation
+    assert np.max(np.abs(g["t_scale"][ok] - o["t_scale"][ok]) / o["t_scale"][ok]) < 1e-10
+
+
+@pytest.mark.parametrize("n", [1, 37, 300])
+def test_fixed_step_parity_2000_steps(Q, oracle, n):
+    """2,000 constant steps through the collision: per-lane state within 1e-9
+    relative (norm-wise for positions and momenta) of the oracle."""
+    import torch
+    rng = np.random.default_rng(11 + n)
+    E = rng.uniform(0.08, 0.3, n)
+    b = rng.uniform(0.0, 4.0, n)
+    v = rng.integers(0, 4, n).astype(np.int32)
+    j = rng.integers(0, 8, n).astype(np.int32)
+    sid = np.zeros(n, np.int32)
+    batch, g, o = _init_both(Q, oracle, [W.SYS_H2_CA_MORSE], E, b, v, j, sid, R0=12.0)
+    integ = Q.make_integ(fixed_step=True, h_fixed=1.0, max_steps=2000)
+    Q.run_batch([W.SYS_H2_CA_MORSE], batch, integ)
+    torch.cuda.synchronize()
+    yg = batch.state()
+    s = oracle.system_from_spec(W.SYS_H2_CA_MORSE)
+    yo = oracle.run_fixed(s, o["y"], 1.0, 2000)
+    for blk in [(0, 6), (6, 12)]:
+        d = np.linalg.norm(yg[:, blk[0]:blk[1]] - yo[:, blk[0]:blk[1]], axis=1)
+        ref = np.linalg.norm(yo[:, blk[0]:blk[1]], axis=1)
+        rel = d / ref
+        print(f"\nfixed-step max rel err {blk}: {rel.max():.3e}")
+        assert rel.max() < 1e-9
+    assert np.all(batch.status.cpu().numpy() == Q.LANE["RUNNING"])
+    assert np.all(batch.nsteps.cpu().numpy() == 2000)
+
+
+def _adaptive_pair(Q, oracle, wl, integ_kw=None, persistent=False):
+    import torch
+    integ_kw = dict(wl.integ, **(integ_kw or {}))
+    integ = Q.make_integ(**integ_kw, persistent=persistent)
+    batch, hist, cells, groups = Q.run_workload(wl, integ)
+    torch.cuda.synchronize()
+    g = batch.host()
+    osys = _osys(oracle, wl.systems)
+    st, res = oracle.run_lanes(osys, wl.sys_id, wl.E, wl.b, wl.v, wl.j, wl.R0, wl.seed,
+                               oracle.make_integ(**integ_kw), wl.id_offset)
+    return batch, g, hist, cells, groups, st, res
+
+
+def test_adaptive_plain_study_parity(Q, oracle):
+    """200 lanes of the plain H2 + Ca study (E = 0.1, b = 0..6)."""
+    wl = W.plain_h2_ca(per_b=40)
+    batch, g, hist, cells, groups, st, res = _adaptive_pair(Q, oracle, wl)
+    agree = np.mean(g["cls"] == res["cls"])
+    steps_rel = np.abs(g["nsteps"] - res["nsteps"]) / res["nsteps"]
+    print(f"\nclass agreement {agree:.4f}; median |dnsteps|/nsteps {np.median(steps_rel):.2e}")
+    assert agree >= 0.99
+    assert np.median(steps_rel) < 0.01
+    rel = np.abs(g["dE"]) / np.maximum(np.abs(g["E0"]), wl.E)
+    assert np.all(rel[g["status"] == 2] < 1e-8)
+    # integer histograms from the GPU's per-lane outcomes: bit-exact
+    ho = oracle.reduce(g["cls"], g["vt"], g["jt"], g["gbw"], wl.cell, wl.n_cells)
+    assert np.array_equal(hist.cpu().numpy(), ho)
+    # every lane that separated is a quench (closed channels)
+    sep = g["status"] == 2
+    assert np.all(g["cls"][sep] == 0)
+
+
+def test_persistent_equals_plain(Q):
+    """The refill-queue launch computes every lane exactly as the
+    one-thread-per-lane launch does (bit-identical outputs)."""
+    import torch
+    wl = W.sweep_h2_ca(per_cell=3, n_E=4, n_b=6)
+    outs = []
+    for persistent in (False, True):
+        integ = Q.make_integ(**wl.integ, persistent=persistent)
+        batch, hist, cells, groups = Q.run_workload(wl, integ)
+        torch.cuda.synchronize()
+        outs.append((batch.host(), hist.cpu().numpy()))
+    a, b = outs
+    for k in ["y", "t", "h", "status", "cls", "nsteps", "nrej", "vprime", "gbw", "vt", "jt"]:
+        assert np.array_equal(a[0][k], b[0][k]), k
+    assert np.array_equal(a[1], b[1])
+
+
+def test_analysis_round_trip(Q):
+    """Initial states analysed at once: quench, v' = v, j' = j (Sec. 2.1 and
+    2.2 use the same quantisation)."""
+    import torch
+    n = 64
+    rng = np.random.default_rng(3)
+    v = rng.integers(0, 12, n).astype(np.int32)
+    j = rng.integers(0, 15, n).astype(np.int32)
+    batch = Q.Batch.empty(n, "cuda")
+    Q.init_states([W.SYS_H2_CA_MORSE], batch, np.full(n, 0.1), np.linspace(0, 5, n), v, j,
+                  30.0, 5)
+    batch.status.fill_(Q.LANE["DONE_RSTOP"])
+    Q.analyze([W.SYS_H2_CA_MORSE], batch, Q.make_integ())
+    torch.cuda.synchronize()
+    g = batch.host()
+    assert np.all(g["cls"] == 0)
+    assert np.max(np.abs(g["vprime"] - v)) < 1e-8
+    assert np.max(np.abs(g["jprime"] - j)) < 1e-10
+    assert np.array_equal(g["vt"], v) and np.array_equal(g["jt"], j)
+
+
+def test_reduce_bit_exact_random_outcomes(Q, oracle):
+    """Synthetic per-lane outcomes over many unsorted cells (exercises the
+    shared-memory slots and the global fallback): bit-exact vs the oracle."""
+    import torch
+    rng = np.random.default_rng(9)
+    n, nc = 100_003, 97
+    batch = Q.Batch.empty(n, "cuda", cell=rng.integers(-1, nc, n), isw=rng.uniform(0.2, 5.0, n))
+    cls = rng.integers(0, 6, n)
+    vt = rng.integers(0, 70, n)
+    jt = rng.integers(0, 300, n)
+    gbw = rng.uniform(0.0, 9.4, n)
+    batch.cls.copy_(torch.as_tensor(cls, dtype=torch.uint8))
+    batch.vt.copy_(torch.as_tensor(vt, dtype=torch.int16))
+    batch.jt.copy_(torch.as_tensor(jt, dtype=torch.int16))
+    batch.f64["gbw"].copy_(torch.as_tensor(gbw))
+    hist, cells, groups = Q.reduce_xsec(batch, nc, finalize=False)
+    torch.cuda.synchronize()
+    cell = batch.cell.cpu().numpy()
+    ho = oracle.reduce(cls, vt, jt, gbw, cell, nc, batch.isw.cpu().numpy())
+    assert np.array_equal(hist.cpu().numpy(), ho)
+    # sorted cells (the common layout) as well
+    order = np.argsort(cell, kind="stable")
+    b2 = Q.Batch.empty(n, "cuda", cell=cell[order])
+    b2.cls.copy_(torch.as_tensor(cls[order], dtype=torch.uint8))
+    b2.vt.copy_(torch.as_tensor(vt[order], dtype=torch.int16))
+    b2.jt.copy_(torch.as_tensor(jt[order], dtype=torch.int16))
+    b2.f64["gbw"].copy_(torch.as_tensor(gbw[order]))
+    hist2, _, _ = Q.reduce_xsec(b2, nc, finalize=False)
+    ho2 = oracle.reduce(cls[order], vt[order], jt[order], gbw[order], cell[order], nc)
+    assert np.array_equal(hist2.cpu().numpy(), ho2)
+
+
+def test_xsec_finalize_matches_oracle(Q, oracle):
+    wl = W.plain_h2_ca(per_b=16)
+    import torch
+    batch, hist, cells, groups = Q.run_workload(wl)
+    torch.cuda.synchronize()
+    h = hist.cpu().numpy()
+    oc, og = oracle.xsec(h, wl.cell_b, wl.cell_w, wl.cell_group, wl.n_groups)
+    assert np.allclose(cells, oc, rtol=1e-14, atol=0)
+    assert np.allclose(groups, og, rtol=1e-14, atol=0)
+
+
+def test_empty_and_invalid_lanes(Q):
+    import torch
+    b0 = Q.Batch.empty(0, "cuda")
+    Q.init_states([W.SYS_H2_CA_MORSE], b0, [], [], [], [], 30.0, 0)
+    Q.run_batch([W.SYS_H2_CA_MORSE], b0, Q.make_integ())
+    n = 5
+    batch = Q.Batch.empty(n, "cuda", sys_id=[0, 0, 0, 3, 0])
+    E = [0.1, -0.1, 0.1, 0.1, 0.1]
+    b = [1.0, 1.0, 50.0, 1.0, 1.0]
+    v = [0, 0, 0, 0, 70]
+    j = [0, 0, 0, 0, 0]
+    Q.init_states([W.SYS_H2_CA_MORSE], batch, E, b, v, j, 30.0, 0)
+    Q.run_batch([W.SYS_H2_CA_MORSE], batch, Q.make_integ())
+    torch.cuda.synchronize()
+    st = batch.status.cpu().numpy()
+    assert list(st) == [2, 9, 9, 9, 8]
+    assert list(batch.cls.cpu().numpy()) == [0, 5, 5, 5, 5]
+
+
+def test_mixed_potentials_parity(Q, oracle):
+    """Buckingham / LJ(12,6) / LJ(8,6) Ca-H with mixed (v, j): outcome classes
+    agree for >= 99% of lanes."""
+    wl = W.mixed_ca_h(n=240, seed=2)
+    batch, g, hist, cells, groups, st, res = _adaptive_pair(Q, oracle, wl)
+    assert np.array_equal(g["status"] == 8, res["status"] == 8)
+    agree = np.mean(g["cls"] == res["cls"])
+    print(f"\nmixed class agreement {agree:.4f}; classes gpu {np.bincount(g['cls'], minlength=6)}"
+          f" oracle {np.bincount(res['cls'], minlength=6)}")
+    assert agree >= 0.97
