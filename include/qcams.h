@@ -318,6 +318,32 @@ typedef struct {
 int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells,
                       int64_t* hist_out, double* xsec_out, void* cuda_stream);
 
+/*
+ * qcams_run_batch without any device allocation.  The paper has no
+ * counterpart: this is a deployment variant for callers that cannot call
+ * cudaMalloc (an application whose device memory all comes from its own pool
+ * or a fixed budget, or that must not let a library allocation synchronise
+ * the device in the middle of its stream work).  Same arguments, outputs and
+ * per-lane semantics as qcams_run_batch.  Its scratch (the potential shape
+ * table and the work counters) lives in one static device array of
+ * QCAMS_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the library
+ * holds until the process exits.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress, with the device current); make this first call
+ *     before any stream capture.
+ *   - Calls on one device share the array and it keeps the last call's
+ *     contents (each call rewrites the shape table and clears the counters
+ *     it uses), so calls that overlap on the GPU race: serialise them on one
+ *     stream.
+ *   - Returns QCAMS_E_CAPACITY if n_sys > QCAMS_NOALLOC_MAX_SYS.  It calls
+ *     no cudaMalloc / cudaFree and no allocating library routine, and does
+ *     not update the statistics read by qcams_last_run_stats.
+ */
+#define QCAMS_NOALLOC_SCRATCH_BYTES 1024
+#define QCAMS_NOALLOC_MAX_SYS 4
+int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
+                            qcams_batch* batch, void* cuda_stream);
+
 /* ---------------------------------------------------------------------- */
 /* Measurement and housekeeping.                                           */
 /* ---------------------------------------------------------------------- */

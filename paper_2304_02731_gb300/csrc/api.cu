@@ -732,6 +732,31 @@ int check_device() {
 }
 
 }  // namespace
+
+// Launch helpers for entry points defined in other translation units.
+int prepare_run(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
+                const qcams_batch* batch, SysSet* ss, IntegParams* ip, DevBatch* d) {
+  int rc = make_sysset(sys, n_sys, ss);
+  if (rc != QCAMS_OK) return rc;
+  if ((rc = make_integ_params(integ, ip)) != QCAMS_OK) return rc;
+  if ((rc = check_batch(batch, !integ->fixed_step)) != QCAMS_OK) return rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  *d = dev_batch(batch);
+  return QCAMS_OK;
+}
+
+cudaError_t launch_shapes(const SysSet& ss, DevShape* shapes, cudaStream_t st) {
+  k_pair_shapes<<<1, 32, 0, st>>>(ss, shapes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_analyze(const SysSet& ss, const DevShape* shapes, double gb_sigma,
+                           const DevBatch& d, cudaStream_t st) {
+  if (d.n == 0) return cudaSuccess;
+  k_analyze<<<(unsigned)((d.n + 127) / 128), 128, 0, st>>>(ss, shapes, gb_sigma, d);
+  return cudaGetLastError();
+}
+
 }  // namespace qcams
 
 using namespace qcams;

@@ -28,6 +28,13 @@ struct IntegParams {
   int fixed_step;
 };
 
+// Validation and launch helpers defined in api.cu.
+int prepare_run(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
+                const qcams_batch* batch, SysSet* ss, IntegParams* ip, DevBatch* d);
+cudaError_t launch_shapes(const SysSet& ss, DevShape* shapes, cudaStream_t st);
+cudaError_t launch_analyze(const SysSet& ss, const DevShape* shapes, double gb_sigma,
+                           const DevBatch& d, cudaStream_t st);
+
 // Launch the integrator over the batch (integrate.cu).
 cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
                              const DevBatch& b, int precision, int persistent, int block,

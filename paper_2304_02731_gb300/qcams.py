@@ -35,7 +35,7 @@ GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
 
 EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
-           "qcams_fma_peak", "qcams_device_info", "qcams_shutdown"]
+           "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc"]
 
 
 class QcamsError(RuntimeError):
@@ -116,6 +116,7 @@ def lib():
                 "qcams_fma_peak": (C.c_int, [I32, P(D), V]),
                 "qcams_device_info": (C.c_int, [P(I32), P(I32), P(I32)]),
                 "qcams_shutdown": (C.c_int, []),
+                "qcams_run_batch_noalloc": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -309,6 +310,14 @@ def run_batch(systems, batch: Batch, integ: Integ, stream=None):
     arr = systems_array(systems)
     _check(lib().qcams_run_batch(arr, len(systems), C.byref(integ), C.byref(batch.c),
                                  _stream(stream)), "qcams_run_batch")
+
+
+def run_batch_noalloc(systems, batch: Batch, integ: Integ, stream=None):
+    """qcams_run_batch_noalloc: qcams_run_batch for callers that must not
+    allocate device memory (scratch in a fixed static device array)."""
+    arr = systems_array(systems)
+    _check(lib().qcams_run_batch_noalloc(arr, len(systems), C.byref(integ), C.byref(batch.c),
+                                         _stream(stream)), "qcams_run_batch_noalloc")
 
 
 def analyze(systems, batch: Batch, integ: Integ, stream=None):

@@ -1,0 +1,66 @@
+"""qcams_run_batch_noalloc: the integrate + analyse entry point for callers
+that cannot allocate device memory (it keeps its scratch in a static device
+array).  Its outputs must equal those of qcams_run_batch on the same
+initial states; two calls in a row check that the shared scratch (shape
+table and counters) is rewritten and cleared between calls.  The same
+lanes give bit-identical results, which satisfies any tolerance the other
+parity tests use."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_2304_02731_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ["y", "t", "h", "status", "cls", "nsteps", "nrej", "dE", "vprime", "jprime", "gbw",
+          "vt", "jt"]
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2304_02731_gb300 import build
+    build.build()
+    from paper_2304_02731_gb300 import qcams
+    qcams.lib()
+    return qcams
+
+
+def _run(Q, wl, entry, persistent):
+    import torch
+    integ = Q.make_integ(**wl.integ, persistent=persistent)
+    batch = Q.Batch.empty(wl.n, "cuda", sys_id=wl.sys_id, cell=wl.cell)
+    Q.init_states(wl.systems, batch, wl.E, wl.b, wl.v, wl.j, wl.R0, wl.seed, wl.id_offset)
+    arr = Q.systems_array(wl.systems)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    fn = getattr(Q.lib(), entry)
+    rc = fn(arr, len(wl.systems), C.byref(integ), C.byref(batch.c), stream)
+    assert rc == 0, Q.lib().qcams_status_string(rc)
+    torch.cuda.synchronize()
+    return batch.host()
+
+
+def test_noalloc_matches_run_batch_on_two_calls(Q):
+    # call 1: all-Morse plain study lanes (persistent launch);
+    # call 2: mixed Buckingham / LJ systems (one thread per lane)
+    cases = [(W.plain_h2_ca(per_b=12), True), (W.mixed_ca_h(n=120, seed=5), False)]
+    for wl, persistent in cases:
+        ref = _run(Q, wl, "qcams_run_batch", persistent)
+        got = _run(Q, wl, "qcams_run_batch_noalloc", persistent)
+        assert np.all(np.isin(got["status"], [2, 3, 8])), got["status"]
+        for k in FIELDS:
+            assert np.array_equal(got[k], ref[k]), k
+
+
+def test_noalloc_rejects_too_many_systems(Q):
+    import torch
+    wl = W.plain_h2_ca(per_b=1)
+    arr = Q.systems_array(wl.systems * 5)
+    batch = Q.Batch.empty(wl.n, "cuda")
+    integ = Q.make_integ()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert Q.lib().qcams_run_batch_noalloc(arr, 5, C.byref(integ), C.byref(batch.c), stream) == -4
