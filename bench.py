@@ -31,10 +31,15 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# Executed FP64 floating-point operations per attempted integrator step
-# (dadd + dmul + 2 dfma, from ncu sass counters on the profile case: see
-# profiles/).  Includes the six right-hand-side evaluations of the step.
-FP64_FLOP_PER_STEP = None  # set from the ncu capture; None -> reported as null
+# FP64 floating-point operations per attempted integrator step of the Morse
+# kernel: 2 dfma + dmul + dadd, from ncu sass counters on the profile case
+# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 594 DFMA,
+# 212 DMUL, 19 DADD per lane-step, six right-hand sides included.
+FP64_FLOP_PER_STEP = 1419
+# DRAM bytes per trajectory of the integrator (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum on the profile case, 686,080 B for 3,840 lanes; the
+# state is loaded once and stored once, everything else is in registers).
+DRAM_BYTES_PER_LANE = 686080 / 3840
 
 
 def parse():
@@ -281,8 +286,9 @@ def run_ours(args):
     ms_max = float(t.item())
     value = world * wl.n * args.steps / (ms_max * 1e-3)
 
-    # one finalised pass for the record (cross sections), outside the timing
-    _, cells, groups = step(finalize=True)
+    # cross sections of the last timed step, for the record (outside the timing)
+    _, cells, groups = Q.reduce_xsec(batch, wl.n_cells, wl.cell_b, wl.cell_w, wl.cell_group,
+                                     wl.n_groups, hist_out=hist, finalize=True)
     torch.cuda.synchronize()
     hb = batch.host()
 
@@ -312,14 +318,14 @@ def run_ours(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hhist.numel() * 8)}
 
     # roofline of the dominant kernel (the integrator): FP64 pipe
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     fp64_peak = Q.fma_peak(64)          # measured here: MEASURED_PEAKS.json has no FP64 figure
     avg_integ_ms = float(np.mean(integ_ms))
     steps_per_launch = steps_total / max(1, args.steps)
     roofline = {"bound": "alu", "unit": "TFLOP/s",
                 "peak": fp64_peak / 1e12,
                 "peak_source": "measured DFMA chain microbenchmark (qcams_fma_peak), this run",
-                "traffic": None}
+                "traffic": DRAM_BYTES_PER_LANE * wl.n if args.workload == "sweep" else None,
+                "traffic_note": "ncu dram bytes of the 3,840-lane profile case scaled by lanes"}
     if FP64_FLOP_PER_STEP:
         ach = FP64_FLOP_PER_STEP * steps_per_launch / (avg_integ_ms * 1e-3)
         roofline.update(achieved=ach / 1e12, frac=ach / fp64_peak,

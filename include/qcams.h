@@ -368,6 +368,15 @@ int qcams_last_run_stats(qcams_run_stats* out, void* cuda_stream);
  */
 int qcams_fma_peak(int32_t precision, double* flops_per_s, void* cuda_stream);
 
+/*
+ * Diagnostic (test support): evaluates, for n device arguments x[i], the
+ * integrator's table-driven exponential (Tang's method, used for the Morse
+ * and Buckingham exponentials) into out_table[i] and CUDA's exp into
+ * out_cuda[i] (device arrays).  Asynchronous.
+ */
+int qcams_debug_exp(const double* x, double* out_table, double* out_cuda, int64_t n,
+                    void* cuda_stream);
+
 /* Device properties used for launch shapes: SM count and CC. */
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);
 

@@ -171,6 +171,18 @@ int make_sysset(const qcams_system* sys, int32_t n_sys, SysSet* out) {
       int rc = make_devpair(in.pair[k], &d.pair[k]);
       if (rc != QCAMS_OK) return rc;
     }
+    // dP1/dt = -(u0 r_AB - cB u1 r_BC + cA u2 r_CA), dP2/dt = -(u1 r_BC + u2 r_CA)
+    d.kf[0] = -d.inv_mu12;
+    d.kf[1] = d.cB * d.inv_mu12;
+    d.kf[2] = -d.cA * d.inv_mu12;
+    d.kf[3] = -d.inv_mu123;
+    d.kf[4] = -d.inv_mu123;
+    const double c2[3] = {d.pair[0].c2, d.pair[1].c2, d.pair[2].c2};
+    d.kf_morse[0] = d.kf[0] * c2[0];
+    d.kf_morse[1] = d.kf[1] * c2[1];
+    d.kf_morse[2] = d.kf[2] * c2[2];
+    d.kf_morse[3] = d.kf[3] * c2[1];
+    d.kf_morse[4] = d.kf[4] * c2[2];
   }
   return QCAMS_OK;
 }
@@ -194,6 +206,8 @@ int make_integ_params(const qcams_integ* in, IntegParams* ip) {
   ip->h_fixed = in->h_fixed;
   ip->max_steps = in->max_steps;
   ip->fixed_step = in->fixed_step ? 1 : 0;
+  ip->rtol_f = (float)in->rtol;
+  ip->atol_f = (float)in->atol;
   return QCAMS_OK;
 }
 
@@ -1044,6 +1058,15 @@ int qcams_last_run_stats(qcams_run_stats* out, void* cuda_stream) {
     if (cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]) == cudaSuccess) out->analyze_ms = b;
   }
   return QCAMS_OK;
+}
+
+int qcams_debug_exp(const double* x, double* out_table, double* out_cuda, int64_t n,
+                    void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !out_table || !out_cuda))) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  if (n == 0) return QCAMS_OK;
+  return cuda_status(launch_exp_check(x, out_table, out_cuda, n, (cudaStream_t)cuda_stream));
 }
 
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor) {

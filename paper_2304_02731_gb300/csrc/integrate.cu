@@ -19,6 +19,15 @@
 //  * Persistent mode: a finished lane takes the next trajectory index from a
 //    device counter, with one atomicAdd per warp for all lanes that need
 //    work (ballot + popc), so warps stay full until the queue drains.
+//  * GB300 issues one warp-wide FP64 instruction per 64 cycles per SM
+//    sub-partition (1/64 of the FP32 rate), so the kernel is bound by the
+//    number of FP64-pipe instructions per step.  Everything that does not
+//    need 53-bit arithmetic runs on the integer / FP32 pipes: the step-size
+//    controller's error norm (magnitudes taken from the doubles' exponent and
+//    leading mantissa bits, ratios in FP32), the stop tests (integer compares
+//    of non-negative doubles) and the minimum-step test (exponent compare).
+//  * The Morse exponential is a table-driven exponential (Tang's method) with
+//    a 256-entry table of 2^(j/256) in shared memory: 10 FP64 instructions.
 #include <cuda_runtime.h>
 
 #include "qcams_device.cuh"
@@ -26,6 +35,50 @@
 
 namespace qcams {
 namespace {
+
+#include "exp2_table.inc"
+
+// e^x by Tang's table-driven method (P. T. P. Tang, ACM Trans. Math. Softw.
+// 15 (1989) 144-157): x = (256 m + j) ln2/256 + r with |r| <= ln2/512, then
+// e^x = 2^m 2^(j/256) e^r with e^r - 1 from its degree-4 Taylor polynomial
+// (truncation < 4e-17 relative).  Arguments below -700 are clamped (e^-700 is
+// ~1e-304, far below any force term); the caller guarantees x < 700.
+__device__ __forceinline__ double texp(double x, const double* __restrict__ T) {
+  const double kShift = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer
+  x = fmax(x, -700.0);
+  const double t = fma(x, kExpInvL, kShift);
+  const int k = __double2loint(t);
+  const double kd = t - kShift;
+  double r = fma(-kd, kExpL1, x);
+  r = fma(-kd, kExpL2, r);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
+  q = fma(q, r, 0.5);
+  q = q * r;
+  const double p = fma(q, r, r);
+  const double Tj = T[k & 255];
+  const double y = fma(Tj, p, Tj);
+  return __hiloint2double(__double2hiint(y) + ((k >> 8) << 20), __double2loint(y));
+}
+
+// |x| as a float, truncated to 20 mantissa bits, using only integer
+// instructions on the high word of x; values below 2^-126 become 0 and
+// values above FLT_MAX saturate.  Sets `bad` for inf / NaN.
+__device__ __forceinline__ float mag_f(double x, unsigned& bad) {
+  const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
+  bad |= (hi >= 0x7ff00000u) ? 1u : 0u;
+  const int e = (int)(hi >> 20) - 896;
+  unsigned bits = ((unsigned)e << 23) | ((hi & 0x000fffffu) << 3);
+  bits = (e <= 0) ? 0u : bits;
+  bits = (e >= 255) ? 0x7f7fffffu : bits;
+  return __uint_as_float(bits);
+}
+__device__ __forceinline__ float signed_f(double x) {
+  unsigned bad = 0;
+  const float m = mag_f(x, bad);
+  return (__double2hiint(x) < 0) ? -m : m;
+}
+// Order of non-negative doubles equals the order of their bit patterns.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 // ---------------------------------------------------------------------------
 // Dormand & Prince (1980) 5(4) tableau (1-based stage indices) and the
@@ -107,32 +160,39 @@ constexpr unsigned FULL = 0xffffffffu;
 //   dV/drho2 = g_BC r_BC + g_CA r_CA,          g = V'(r)/r.
 // ---------------------------------------------------------------------------
 template <bool MORSE>
-__device__ __forceinline__ double pair_g(const DevPair& q, double s) {
-  double ri = rsqrt(s);
-  double r = s * ri;
+__device__ __forceinline__ double pair_u(const DevPair& q, double s, const double* __restrict__ T) {
+  const double ri = rsqrt(s);
+  const double r = s * ri;
   if (MORSE) {
-    double x = exp(fma(-q.c0, r, q.c1));
-    return q.c2 * x * (1.0 - x) * ri;
+    // u = x (1 - x) / r, x = e^{-alpha (r - re)}; the factor 2 alpha De is in kf_morse
+    const double x = texp(fma(-q.c0, r, q.c1), T);
+    return fma(-x, x, x) * ri;
   }
   return pot_g(q, ri, r);
 }
 
 template <bool MORSE>
-__device__ __forceinline__ void accel(const DevSys& S, const double* x, double* a, double* s2) {
-  double rab0 = x[0], rab1 = x[1], rab2 = x[2];
-  double rbc0 = fma(-S.cB, x[0], x[3]), rbc1 = fma(-S.cB, x[1], x[4]), rbc2 = fma(-S.cB, x[2], x[5]);
-  double rca0 = fma(S.cA, x[0], x[3]), rca1 = fma(S.cA, x[1], x[4]), rca2 = fma(S.cA, x[2], x[5]);
+__device__ __forceinline__ void accel(const DevSys& S, const double* __restrict__ T,
+                                      const double* x, double* a, double* s2) {
+  const double rab0 = x[0], rab1 = x[1], rab2 = x[2];
+  const double rbc0 = fma(-S.cB, x[0], x[3]), rbc1 = fma(-S.cB, x[1], x[4]),
+               rbc2 = fma(-S.cB, x[2], x[5]);
+  const double rca0 = fma(S.cA, x[0], x[3]), rca1 = fma(S.cA, x[1], x[4]),
+               rca2 = fma(S.cA, x[2], x[5]);
   s2[0] = fma(rab0, rab0, fma(rab1, rab1, rab2 * rab2));
   s2[1] = fma(rbc0, rbc0, fma(rbc1, rbc1, rbc2 * rbc2));
   s2[2] = fma(rca0, rca0, fma(rca1, rca1, rca2 * rca2));
-  double g0 = pair_g<MORSE>(S.pair[0], s2[0]);
-  double g1 = pair_g<MORSE>(S.pair[1], s2[1]);
-  double g2 = pair_g<MORSE>(S.pair[2], s2[2]);
-  double f0 = -g0 * S.inv_mu12, f1 = S.cB * g1 * S.inv_mu12, f2 = -S.cA * g2 * S.inv_mu12;
+  const double u0 = pair_u<MORSE>(S.pair[0], s2[0], T);
+  const double u1 = pair_u<MORSE>(S.pair[1], s2[1], T);
+  const double u2 = pair_u<MORSE>(S.pair[2], s2[2], T);
+  const double f0 = (MORSE ? S.kf_morse[0] : S.kf[0]) * u0;
+  const double f1 = (MORSE ? S.kf_morse[1] : S.kf[1]) * u1;
+  const double f2 = (MORSE ? S.kf_morse[2] : S.kf[2]) * u2;
+  const double h1 = (MORSE ? S.kf_morse[3] : S.kf[3]) * u1;
+  const double h2 = (MORSE ? S.kf_morse[4] : S.kf[4]) * u2;
   a[0] = fma(f0, rab0, fma(f1, rbc0, f2 * rca0));
   a[1] = fma(f0, rab1, fma(f1, rbc1, f2 * rca1));
   a[2] = fma(f0, rab2, fma(f1, rbc2, f2 * rca2));
-  double h1 = -g1 * S.inv_mu123, h2 = -g2 * S.inv_mu123;
   a[3] = fma(h1, rbc0, h2 * rca0);
   a[4] = fma(h1, rbc1, h2 * rca1);
   a[5] = fma(h1, rbc2, h2 * rca2);
@@ -157,23 +217,24 @@ __device__ __forceinline__ void stage_x(const double* rho, const double* vel, co
 // solution (acc[6] = a(xn), FSAL), er / ev the embedded error estimates of
 // positions and velocities, s2 the squared pair distances at xn.
 template <bool MORSE>
-__device__ __forceinline__ void dp_step(const DevSys& S, const double* rho, const double* vel,
-                                        double (*acc)[6], double h, double* xn, double* vn,
-                                        double* er, double* ev, double* s2) {
+__device__ __forceinline__ void dp_step(const DevSys& S, const double* __restrict__ T,
+                                        const double* rho, const double* vel, double (*acc)[6],
+                                        double h, double* xn, double* vn, double* er, double* ev,
+                                        double* s2) {
   const double hh = h * h;
   double x[6];
   stage_x<2>(rho, vel, acc, h, hh, x);
-  accel<MORSE>(S, x, acc[1], s2);
+  accel<MORSE>(S, T, x, acc[1], s2);
   stage_x<3>(rho, vel, acc, h, hh, x);
-  accel<MORSE>(S, x, acc[2], s2);
+  accel<MORSE>(S, T, x, acc[2], s2);
   stage_x<4>(rho, vel, acc, h, hh, x);
-  accel<MORSE>(S, x, acc[3], s2);
+  accel<MORSE>(S, T, x, acc[3], s2);
   stage_x<5>(rho, vel, acc, h, hh, x);
-  accel<MORSE>(S, x, acc[4], s2);
+  accel<MORSE>(S, T, x, acc[4], s2);
   stage_x<6>(rho, vel, acc, h, hh, x);
-  accel<MORSE>(S, x, acc[5], s2);
+  accel<MORSE>(S, T, x, acc[5], s2);
   stage_x<7>(rho, vel, acc, h, hh, xn);
-  accel<MORSE>(S, xn, acc[6], s2);
+  accel<MORSE>(S, T, xn, acc[6], s2);
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     double vb = kT.b[1] * acc[0][i];
@@ -199,23 +260,16 @@ struct LaneState {
   int nacc, nrej, calls;   // calls = accepted + rejected in this launch
   int status;
   int sid;
+  float atv[2];            // atol / mu of the two velocity blocks (FP32)
   bool rejected;           // the current step attempt follows a rejection
 };
 
-__device__ __forceinline__ double rms_ratio(const double* e, const double* sc) {
-  double s = 0.0;
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    double q = e[i] / sc[i];
-    s = fma(q, q, s);
-  }
-  return s;
-}
-
 // Starting step (Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.4), as
-// used by SciPy's solve_ivp; error-estimator order 4, exponent 1/5.
+// used by SciPy's solve_ivp; error-estimator order 4, exponent 1/5.  Run once
+// per trajectory, in FP64.
 template <bool MORSE>
-__device__ double initial_step(const DevSys& S, const LaneState& L, double rtol, double atol) {
+__device__ double initial_step(const DevSys& S, const double* __restrict__ T, const LaneState& L,
+                               double rtol, double atol) {
   double atv[2] = {atol * S.inv_mu12, atol * S.inv_mu123};
   double d0 = 0.0, d1 = 0.0;
 #pragma unroll
@@ -233,7 +287,7 @@ __device__ double initial_step(const DevSys& S, const LaneState& L, double rtol,
   double x1[6], a1[6], s2[3];
 #pragma unroll
   for (int i = 0; i < 6; ++i) x1[i] = fma(h0, L.vel[i], L.rho[i]);
-  accel<MORSE>(S, x1, a1, s2);
+  accel<MORSE>(S, T, x1, a1, s2);
   double d2 = 0.0;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -255,8 +309,9 @@ __device__ __forceinline__ bool runnable(int st) {
 // Load lane i; returns false if it is not runnable.  Computes acc[0] and,
 // if no step size is stored yet, the starting step.
 template <bool MORSE>
-__device__ bool lane_load(const SysSet& sys, const IntegParams& ip, const DevBatch& B, int64_t i,
-                          LaneState& L, unsigned long long& rhs_count) {
+__device__ bool lane_load(const SysSet& sys, const IntegParams& ip, const double* __restrict__ T,
+                          const DevBatch& B, int64_t i, LaneState& L,
+                          unsigned long long& rhs_count) {
   L.status = B.status[i];
   if (!runnable(L.status)) return false;
   L.sid = B.sys_id[i];
@@ -280,11 +335,13 @@ __device__ bool lane_load(const SysSet& sys, const IntegParams& ip, const DevBat
   L.calls = 0;
   L.rejected = false;
   L.status = QCAMS_LANE_RUNNING;
+  L.atv[0] = (float)(ip.atol * S.inv_mu12);
+  L.atv[1] = (float)(ip.atol * S.inv_mu123);
   double s2[3];
-  accel<MORSE>(S, L.rho, L.acc[0], s2);
+  accel<MORSE>(S, T, L.rho, L.acc[0], s2);
   rhs_count += 1;
   if (!(L.h > 0.0)) {
-    L.h = initial_step<MORSE>(S, L, ip.rtol, ip.atol);
+    L.h = initial_step<MORSE>(S, T, L, ip.rtol, ip.atol);
     rhs_count += 1;
   }
   return true;
@@ -311,66 +368,85 @@ __device__ void lane_store(const SysSet& sys, const DevBatch& B, int64_t i, cons
 // scale atol + rtol max(|y_n|, |y_n+1|); accept iff norm < 1; new step
 // h * clamp(0.9 norm^(-1/5), 0.2, 10), with no growth on the attempt that
 // follows a rejection.  After an accepted step the stop rules are applied
-// (Sec. 3.1: r_stop while separating, or t >= t_max).  The controller's
-// power is taken in FP32 (its result only scales the next step).
+// (Sec. 3.1: r_stop while separating, or t >= t_max).
+//
+// Only the step itself (stages, update, error vector) is FP64.  The norm is
+// formed in FP32 from 20-bit magnitudes of the error, state and scale terms
+// (relative error < 1e-6, irrelevant to a step-size controller); accept /
+// reject is a select, so the warp does not diverge.  The minimum step is
+// checked by exponents: h fails below 8-16 ulp(t).
 template <bool MORSE>
 __device__ __forceinline__ void lane_attempt(const SysSet& sys, const DevShape* shapes,
-                                             const IntegParams& ip, LaneState& L) {
+                                             const IntegParams& ip, const double* __restrict__ T,
+                                             LaneState& L) {
   const DevSys& S = sys.s[L.sid];
-  // minimum step: 10 ulp(t)
-  double ulp_t = __longlong_as_double(__double_as_longlong(L.t) + 1) - L.t;
-  if (L.h < 10.0 * ulp_t) {
-    L.status = QCAMS_LANE_FAIL_HMIN;
-    return;
+  {
+    const int eh = (__double2hiint(L.h) >> 20) & 0x7ff;
+    const int et = (__double2hiint(L.t) >> 20) & 0x7ff;
+    if (et - eh >= 49 || eh == 0) {
+      L.status = QCAMS_LANE_FAIL_HMIN;
+      return;
+    }
   }
   double xn[6], vn[6], er[6], ev[6], s2[3];
-  dp_step<MORSE>(S, L.rho, L.vel, L.acc, L.h, xn, vn, er, ev, s2);
-  double sr[6], sv[6];
-  const double atv0 = ip.atol * S.inv_mu12, atv1 = ip.atol * S.inv_mu123;
+  dp_step<MORSE>(S, T, L.rho, L.vel, L.acc, L.h, xn, vn, er, ev, s2);
+  unsigned bad = 0, ignore = 0;
+  float sum = 0.f;
+  const float rt = ip.rtol_f, at = ip.atol_f;
+  const float atv0 = L.atv[0], atv1 = L.atv[1];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    sr[i] = fma(ip.rtol, fmax(fabs(L.rho[i]), fabs(xn[i])), ip.atol);
-    sv[i] = fma(ip.rtol, fmax(fabs(L.vel[i]), fabs(vn[i])), i < 3 ? atv0 : atv1);
+    const float scr = fmaf(rt, fmaxf(mag_f(L.rho[i], ignore), mag_f(xn[i], ignore)), at);
+    const float qr = __fdividef(mag_f(er[i], bad), scr);
+    sum = fmaf(qr, qr, sum);
+    const float scv = fmaf(rt, fmaxf(mag_f(L.vel[i], ignore), mag_f(vn[i], ignore)),
+                           i < 3 ? atv0 : atv1);
+    const float qv = __fdividef(mag_f(ev[i], bad), scv);
+    sum = fmaf(qv, qv, sum);
   }
-  double en2 = (rms_ratio(er, sr) + rms_ratio(ev, sv)) * (1.0 / 12.0);
+  const float en2 = sum * (1.0f / 12.0f);
   L.calls += 1;
-  if (!(en2 == en2)) {
+  if (bad) {
     L.status = QCAMS_LANE_FAIL_NAN;
     return;
   }
   // en^(-1/5) = en2^(-1/10)
-  float fac = __powf(static_cast<float>(en2), -0.1f) * 0.9f;
-  bool accept = en2 < 1.0;
-  if (accept) {
-    float f = (en2 == 0.0) ? 10.0f : fminf(10.0f, fac);
-    if (L.rejected) f = fminf(1.0f, f);
-    L.t += L.h;
-    L.h *= static_cast<double>(f);
+  const float fac = 0.9f * __powf(en2, -0.1f);
+  const bool accept = en2 < 1.0f;
+  float fa = (en2 == 0.0f) ? 10.0f : fminf(10.0f, fac);
+  fa = L.rejected ? fminf(1.0f, fa) : fa;
+  const float f = accept ? fa : fmaxf(0.2f, fac);
+  const double tn = L.t + L.h;
+  L.t = accept ? tn : L.t;
+  L.h = L.h * static_cast<double>(f);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      L.rho[i] = xn[i];
-      L.vel[i] = vn[i];
-      L.acc[0][i] = L.acc[6][i];
-    }
-    L.nacc += 1;
-    L.rejected = false;
-    // stop rules
-    bool collapse = false;
-    double smax = fmax(s2[0], fmax(s2[1], s2[2]));
+  for (int i = 0; i < 6; ++i) {
+    L.rho[i] = accept ? xn[i] : L.rho[i];
+    L.vel[i] = accept ? vn[i] : L.vel[i];
+    L.acc[0][i] = accept ? L.acc[6][i] : L.acc[0][i];
+  }
+  L.nacc += accept ? 1 : 0;
+  L.nrej += accept ? 0 : 1;
+  L.rejected = !accept;
+  // stop rules on the accepted state (integer / FP32 compares)
+  const long long smax = max(dbits(s2[0]), max(dbits(s2[1]), dbits(s2[2])));
+  const float radial = fmaf(signed_f(L.rho[3]), signed_f(L.vel[3]),
+                            fmaf(signed_f(L.rho[4]), signed_f(L.vel[4]),
+                                 signed_f(L.rho[5]) * signed_f(L.vel[5])));
+  bool collapse = false;
+  if (!MORSE) {
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-      if (S.pair[k].kind == QCAMS_BUCK && s2[k] < shapes[L.sid * 3 + k].r_b2) collapse = true;
-    double radial = L.rho[3] * L.vel[3] + L.rho[4] * L.vel[4] + L.rho[5] * L.vel[5];
-    if (collapse) L.status = QCAMS_LANE_FAIL_COLLAPSE;
-    else if (smax > ip.r_stop2 && radial > 0.0) L.status = QCAMS_LANE_DONE_RSTOP;
-    else if (L.t >= L.tmax) L.status = QCAMS_LANE_DONE_TMAX;
-  } else {
-    L.h *= static_cast<double>(fmaxf(0.2f, fac));
-    L.nrej += 1;
-    L.rejected = true;
+      collapse |= S.pair[k].kind == QCAMS_BUCK &&
+                  dbits(s2[k]) < dbits(shapes[L.sid * 3 + k].r_b2);
   }
-  if (L.status == QCAMS_LANE_RUNNING && (long long)(L.nacc + L.nrej) >= ip.max_steps)
-    L.status = QCAMS_LANE_FAIL_MAXSTEPS;
+  int st = L.status;
+  st = (accept && dbits(L.t) >= dbits(L.tmax)) ? QCAMS_LANE_DONE_TMAX : st;
+  st = (accept && smax > dbits(ip.r_stop2) && radial > 0.0f) ? QCAMS_LANE_DONE_RSTOP : st;
+  st = (accept && collapse) ? QCAMS_LANE_FAIL_COLLAPSE : st;
+  st = (st == QCAMS_LANE_RUNNING && (long long)(L.nacc + L.nrej) >= ip.max_steps)
+           ? QCAMS_LANE_FAIL_MAXSTEPS : st;
+  L.status = st;
 }
 
 __device__ __forceinline__ void flush_counters(unsigned long long rhs, unsigned long long steps,
@@ -386,16 +462,24 @@ __device__ __forceinline__ void flush_counters(unsigned long long rhs, unsigned 
   }
 }
 
+// Stage the exponential table in shared memory (2 KB per block).
+__device__ __forceinline__ void load_exp_table(double* sT) {
+  for (int k = threadIdx.x; k < 256; k += blockDim.x) sT[k] = kExp2Table[k];
+  __syncthreads();
+}
+
 // One thread per trajectory.
 template <bool MORSE>
 __global__ void __launch_bounds__(128) k_integrate_plain(SysSet sys, const DevShape* shapes,
                                                          IntegParams ip, DevBatch B,
                                                          unsigned long long* counters) {
+  __shared__ double sT[256];
+  load_exp_table(sT);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long rhs = 0, steps = 0;
   LaneState L;
-  if (i < B.n && lane_load<MORSE>(sys, ip, B, i, L, rhs)) {
-    while (L.status == QCAMS_LANE_RUNNING) lane_attempt<MORSE>(sys, shapes, ip, L);
+  if (i < B.n && lane_load<MORSE>(sys, ip, sT, B, i, L, rhs)) {
+    while (L.status == QCAMS_LANE_RUNNING) lane_attempt<MORSE>(sys, shapes, ip, sT, L);
     rhs += 6ull * L.calls;
     steps += L.calls;
     lane_store<MORSE>(sys, B, i, L);
@@ -409,6 +493,8 @@ template <bool MORSE>
 __global__ void __launch_bounds__(128) k_integrate_persistent(SysSet sys, const DevShape* shapes,
                                                               IntegParams ip, DevBatch B,
                                                               unsigned long long* counters) {
+  __shared__ double sT[256];
+  load_exp_table(sT);
   const unsigned lane = threadIdx.x & 31u;
   unsigned long long rhs = 0, steps = 0;
   LaneState L;
@@ -428,13 +514,13 @@ __global__ void __launch_bounds__(128) k_integrate_persistent(SysSet sys, const 
           exhausted = true;
         } else {
           idx = k;
-          have = lane_load<MORSE>(sys, ip, B, idx, L, rhs);
+          have = lane_load<MORSE>(sys, ip, sT, B, idx, L, rhs);
         }
       }
     }
     if (__all_sync(FULL, exhausted && !have)) break;
     if (have) {
-      lane_attempt<MORSE>(sys, shapes, ip, L);
+      lane_attempt<MORSE>(sys, shapes, ip, sT, L);
       if (L.status != QCAMS_LANE_RUNNING) {
         rhs += 6ull * L.calls;
         steps += L.calls;
@@ -451,6 +537,8 @@ __global__ void __launch_bounds__(128) k_integrate_persistent(SysSet sys, const 
 template <bool MORSE>
 __global__ void __launch_bounds__(128) k_integrate_fixed(SysSet sys, IntegParams ip, DevBatch B,
                                                          unsigned long long* counters) {
+  __shared__ double sT[256];
+  load_exp_table(sT);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long rhs = 0, steps = 0;
   if (i < B.n) {
@@ -469,12 +557,12 @@ __global__ void __launch_bounds__(128) k_integrate_fixed(SysSet sys, IntegParams
         L.vel[3 + k] = B.y[9 + k][i] * S.inv_mu123;
       }
       double s2[3];
-      accel<MORSE>(S, L.rho, L.acc[0], s2);
+      accel<MORSE>(S, sT, L.rho, L.acc[0], s2);
       double t = B.t[i];
       const double h = ip.h_fixed;
       for (long long it = 0; it < ip.max_steps; ++it) {
         double xn[6], vn[6], er[6], ev[6];
-        dp_step<MORSE>(S, L.rho, L.vel, L.acc, h, xn, vn, er, ev, s2);
+        dp_step<MORSE>(S, sT, L.rho, L.vel, L.acc, h, xn, vn, er, ev, s2);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           L.rho[q] = xn[q];
@@ -494,6 +582,15 @@ __global__ void __launch_bounds__(128) k_integrate_fixed(SysSet sys, IntegParams
     }
   }
   flush_counters(rhs, steps, counters);
+}
+
+__global__ void k_exp_check(const double* x, double* mine, double* ref, long long n) {
+  __shared__ double sT[256];
+  load_exp_table(sT);
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  mine[i] = texp(x[i], sT);
+  ref[i] = exp(x[i]);
 }
 
 bool all_morse(const SysSet& s) {
@@ -540,6 +637,12 @@ cudaError_t launch_fp64(const SysSet& sys, const DevShape* shapes, const IntegPa
 }
 
 }  // namespace
+
+cudaError_t launch_exp_check(const double* x, double* mine, double* ref, long long n,
+                             cudaStream_t st) {
+  k_exp_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, mine, ref, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
                              const DevBatch& b, int precision, int persistent, int block,

@@ -35,6 +35,12 @@ struct DevSys {
   double cA, cB;               // cA = mB/(mA+mB), cB = mA/(mA+mB)
   double mu_pair[3];           // reduced masses of the pairs AB, BC, CA
   DevPair pair[3];             // AB, BC, CA
+  // Force coefficients: with u_k = V_k'(r_k)/r_k (generic) the accelerations
+  // are a1 = kf[0] u0 r_AB + kf[1] u1 r_BC + kf[2] u2 r_CA and
+  // a2 = kf[3] u1 r_BC + kf[4] u2 r_CA; kf_morse[] additionally folds the
+  // Morse factor 2 alpha De, so that u_k = x(1 - x)/r with x = e^{-alpha(r-re)}.
+  double kf[5];
+  double kf_morse[5];
 };
 
 struct SysSet {

@@ -26,7 +26,13 @@ struct IntegParams {
   double rtol, atol, r_stop2, t_stop, h_fixed;
   long long max_steps;
   int fixed_step;
+  float rtol_f, atol_f;  // error-norm constants in FP32
 };
+
+// Diagnostic: the integrator's table-driven exponential and CUDA's exp on n
+// device arguments (integrate.cu; used by the accuracy test).
+cudaError_t launch_exp_check(const double* x, double* mine, double* ref, long long n,
+                             cudaStream_t st);
 
 // Validation and launch helpers defined in api.cu.
 int prepare_run(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,

@@ -35,7 +35,8 @@ GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
 
 EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
-           "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc"]
+           "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
+           "qcams_debug_exp"]
 
 
 class QcamsError(RuntimeError):
@@ -117,6 +118,7 @@ def lib():
                 "qcams_device_info": (C.c_int, [P(I32), P(I32), P(I32)]),
                 "qcams_shutdown": (C.c_int, []),
                 "qcams_run_batch_noalloc": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
+                "qcams_debug_exp": (C.c_int, [V, V, V, I64, V]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -370,6 +372,15 @@ def fma_peak(precision: int = 64, stream=None) -> float:
     f = C.c_double()
     _check(lib().qcams_fma_peak(int(precision), C.byref(f), _stream(stream)), "qcams_fma_peak")
     return f.value
+
+
+def debug_exp(x: torch.Tensor, stream=None):
+    """qcams_debug_exp: (table-driven exp, CUDA exp) of the device tensor x."""
+    x = x.to(torch.float64).contiguous()
+    a, b = torch.empty_like(x), torch.empty_like(x)
+    _check(lib().qcams_debug_exp(x.data_ptr(), a.data_ptr(), b.data_ptr(), x.numel(),
+                                 _stream(stream)), "qcams_debug_exp")
+    return a, b
 
 
 def device_info():

@@ -268,3 +268,19 @@ def test_mixed_potentials_parity(Q, oracle):
     print(f"\nmixed class agreement {agree:.4f}; classes gpu {np.bincount(g['cls'], minlength=6)}"
           f" oracle {np.bincount(res['cls'], minlength=6)}")
     assert agree >= 0.97
+
+
+def test_table_exp_matches_cuda_exp(Q):
+    """The integrator's table-driven exponential agrees with CUDA's exp to
+    within 2 ulp over the arguments the potentials produce."""
+    import torch
+    g = torch.Generator(device="cpu").manual_seed(1)
+    x = torch.cat([torch.rand(2_000_000, generator=g, dtype=torch.float64) * 750 - 700,
+                   torch.linspace(-5, 5, 100_001, dtype=torch.float64)]).cuda()
+    mine, ref = Q.debug_exp(x)
+    rel = ((mine - ref).abs() / ref).max().item()
+    print(f"\ntable exp max rel diff vs CUDA exp: {rel:.3e}")
+    assert rel <= 2 * 2.220446049250313e-16
+    lo = torch.tensor([-701.0, -800.0, -1e6], dtype=torch.float64, device="cuda")
+    m2, r2 = Q.debug_exp(lo)
+    assert torch.all(m2 > 0) and torch.all(m2 < 1e-303)
