@@ -54,8 +54,16 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0,
                     help="use a stratified subset of this many lanes (profiling runs)")
     ap.add_argument("--max-steps", type=int, default=1_000_000)
+    ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
+                    help="32: FP32 integrator with Kahan-compensated updates "
+                         "(rtol 1e-6, atol 1e-8), FP64 everywhere else")
     ap.add_argument("--persistent", type=int, default=1)
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--tune", type=int, default=1,
+                    help="pick the launch shape with qcams_autotune before timing")
+    ap.add_argument("--graph", type=int, default=1,
+                    help="capture the step (init, run, reduce) in a CUDA graph")
     ap.add_argument("--cpu-per-cell", type=int, default=8,
                     help="oracle sample for cpu_baseline: lanes per cell")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -74,6 +82,9 @@ def make_workload(args):
     if args.lanes and args.lanes < wl.n:
         per = max(1, args.lanes // wl.n_cells)
         wl = wl.take(W.stratified(wl, per))
+    if getattr(args, "precision", 64) == 32:
+        wl.integ = dict(W.INTEG_FP32)
+        wl.name += "_fp32"
     return wl
 
 
@@ -239,7 +250,23 @@ def run_ours(args):
     wl = make_workload(args)
     wl.id_offset = rank * wl.n          # weak scaling: each rank its own trajectory ids
     integ = Q.make_integ(**wl.integ, persistent=bool(args.persistent), block=args.block,
-                         max_steps=args.max_steps)
+                         blocks_per_sm=args.blocks_per_sm, max_steps=args.max_steps,
+                         precision=args.precision)
+    tune = None
+    if args.tune and args.persistent and args.precision == 64:
+        # launch shape measured on a stratified sample of the workload
+        from paper_2304_02731_gb300 import workloads as W
+        per = max(1, min(256, wl.n // wl.n_cells))
+        sw = wl.take(W.stratified(wl, per))
+        sb = Q.Batch.empty(sw.n, dev, sys_id=sw.sys_id, cell=sw.cell, keep_u=False)
+        Q.init_states(sw.systems, sb, sw.E, sw.b, sw.v, sw.j, sw.R0, sw.seed, sw.id_offset)
+        best, table = Q.autotune(sw.systems, sb, integ, max_attempts=1500)
+        integ = best
+        tune = {"sample_lanes": sw.n, "max_attempts": 1500,
+                "chosen": {"block": best.block, "blocks_per_sm": best.blocks_per_sm},
+                "variants": [{k: (round(v, 4) if isinstance(v, float) else v)
+                              for k, v in r.items()} for r in table]}
+        del sb
     batch = Q.Batch.empty(wl.n, dev, sys_id=wl.sys_id, cell=wl.cell, keep_u=False)
     E_d = torch.as_tensor(wl.E, device=dev)
     b_d = torch.as_tensor(wl.b, device=dev)
@@ -257,6 +284,15 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    graph = None
+    if args.graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+        run_step = graph.replay
+    else:
+        run_step = step
 
     def barrier():
         if world > 1:
@@ -269,9 +305,10 @@ def run_ours(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     integ_ms, steps_total, rhs_total = [], 0, 0
+    stream = torch.cuda.current_stream()
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        run_step()
         st = Q.last_run_stats()          # synchronises; read after each step's run
         integ_ms.append(st["integrate_ms"])
         steps_total += st["steps"]
@@ -326,7 +363,7 @@ def run_ours(args):
                 "peak_source": "measured DFMA chain microbenchmark (qcams_fma_peak), this run",
                 "traffic": DRAM_BYTES_PER_LANE * wl.n if args.workload == "sweep" else None,
                 "traffic_note": "ncu dram bytes of the 3,840-lane profile case scaled by lanes"}
-    if FP64_FLOP_PER_STEP:
+    if FP64_FLOP_PER_STEP and args.precision == 64:
         ach = FP64_FLOP_PER_STEP * steps_per_launch / (avg_integ_ms * 1e-3)
         roofline.update(achieved=ach / 1e12, frac=ach / fp64_peak,
                         flop_per_step=FP64_FLOP_PER_STEP)
@@ -344,12 +381,16 @@ def run_ours(args):
 
     cls_counts = np.bincount(hb["cls"], minlength=6).tolist()
     line = {
-        "metric": "trajectories/s (H2+Ca, FP64 RK45)", "value": value,
+        "metric": f"trajectories/s (H2+Ca, FP{args.precision} RK45)", "value": value,
         "unit": "trajectories/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": f"f{args.precision}",
+        "data": "synthetic",
         "config": {"workload": wl.name, "trajectories_per_gpu": wl.n,
-                   "launch": "persistent refill queue" if args.persistent else "one thread/lane",
+                   "launch": ("persistent refill queue" if args.persistent else "one thread/lane")
+                   + (", CUDA graph" if graph is not None else "")
+                   + f", block {integ.block or 128} x {integ.blocks_per_sm or 1}/SM variant",
+                   "autotune": tune,
                    "rtol": wl.integ["rtol"], "atol": wl.integ["atol"],
                    "l2": "inputs larger than L2 (SoA state > 129 MB)",
                    "parallelism": f"replicas x{world}"},

@@ -137,8 +137,14 @@ typedef struct {
   int32_t persistent;  /* 1 = persistent refill-queue launch (finished lanes
                           take the next trajectory from a device counter);
                           0 = one thread per trajectory */
-  int32_t block;       /* threads per block (0 = library default) */
-  int32_t blocks_per_sm; /* persistent grid size per SM (0 = from occupancy) */
+  int32_t block;       /* threads per block (0 = 128) */
+  int32_t blocks_per_sm; /* resident blocks per SM the integrator variant is
+                            compiled for (its __launch_bounds__ minimum, which
+                            caps registers per thread; 0 = 1).  Supported
+                            (block, blocks_per_sm): (128,1) (64,1) (128,3)
+                            (64,6) (64,7) (256,1); qcams_autotune picks one.
+                            The persistent grid is the resulting occupancy
+                            times the SM count. */
   int32_t pad;
 } qcams_integ;
 
@@ -343,6 +349,31 @@ int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells,
 #define QCAMS_NOALLOC_MAX_SYS 4
 int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
                             qcams_batch* batch, void* cuda_stream);
+
+/*
+ * Launch-shape autotuner for the persistent integrator (the paper has no
+ * counterpart; it sizes the GPU launch).  `sample` is an initialised batch
+ * (device SoA, status READY) representative of the workload; for every
+ * supported (block, blocks_per_sm) variant the integrator runs on it, from
+ * the same saved initial state, with at most `max_attempts` step attempts
+ * per lane, and the attempted lane-steps per second are measured with CUDA
+ * events.  The sample's state is restored afterwards.  results (host, room
+ * for QCAMS_TUNE_MAX_VARIANTS entries) receives one entry per variant,
+ * *n_results their number, and *best a copy of *integ with the fastest
+ * shape and persistent = 1.  Synchronous; allocates a temporary copy of the
+ * sample state (~121 bytes per lane) with cudaMallocAsync.
+ */
+#define QCAMS_TUNE_MAX_VARIANTS 16
+typedef struct {
+  int32_t block, blocks_per_sm;  /* the variant */
+  int32_t regs;                  /* registers per thread */
+  int32_t resident_blocks;       /* occupancy: blocks per SM */
+  double ms;                     /* integrator time on the sample */
+  double lane_steps_per_s;       /* attempted lane-steps per second */
+} qcams_tune_result;
+int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
+                   qcams_batch* sample, int64_t max_attempts, qcams_tune_result* results,
+                   int32_t* n_results, qcams_integ* best, void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
 /* Measurement and housekeeping.                                           */

@@ -197,8 +197,11 @@ int make_integ_params(const qcams_integ* in, IntegParams* ip) {
     if (!finite_pos(in->r_stop) || !finite_pos(in->t_stop) || in->max_steps < 1)
       return QCAMS_E_INVALID;
   }
-  if (in->precision != 64 && in->precision != 0) return QCAMS_E_INVALID;
+  if (in->precision != 64 && in->precision != 32 && in->precision != 0) return QCAMS_E_INVALID;
+  if (in->precision == 32 && in->fixed_step) return QCAMS_E_INVALID;
   if (in->block < 0 || in->block > 1024 || in->blocks_per_sm < 0) return QCAMS_E_INVALID;
+  if (!in->fixed_step && !integrate_shape_supported(in->block, in->blocks_per_sm))
+    return QCAMS_E_INVALID;
   ip->rtol = in->rtol;
   ip->atol = in->atol;
   ip->r_stop2 = in->r_stop * in->r_stop;
@@ -734,6 +737,21 @@ __global__ void __launch_bounds__(kReduceBlock) k_reduce(DevBatch B, int n_cells
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? QCAMS_OK : QCAMS_E_CUDA; }
 
+// Event record that also times graph replays: while the stream is being
+// captured, an external record node is added to the graph.
+cudaError_t record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  return cudaEventRecord(ev, st);
+}
+
+// Drop a non-sticky error left by an earlier, unrelated runtime call, so that
+// the cudaGetLastError() after this call's launches reports only its own.
+void clear_stale_error() { (void)cudaGetLastError(); }
+
 int check_device() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QCAMS_E_NODEVICE;
@@ -847,6 +865,7 @@ int qcams_system_setup(const double mass_u[3], const int32_t kind[3], const doub
 
 int qcams_levels(const qcams_system* sys, int32_t n_sys, const int32_t* sys_id, const int32_t* v,
                  const int32_t* j, int32_t n_levels, qcams_level* out, void* cuda_stream) {
+  clear_stale_error();
   SysSet ss;
   int rc = make_sysset(sys, n_sys, &ss);
   if (rc != QCAMS_OK) return rc;
@@ -887,6 +906,7 @@ int qcams_init_states(const qcams_system* sys, int32_t n_sys, const double* E_co
                       const int32_t* v, const int32_t* j, double R0, uint64_t seed,
                       uint64_t id_offset, const double* const* u_in, qcams_batch* batch,
                       void* cuda_stream) {
+  clear_stale_error();
   SysSet ss;
   int rc = make_sysset(sys, n_sys, &ss);
   if (rc != QCAMS_OK) return rc;
@@ -916,6 +936,7 @@ int qcams_init_states(const qcams_system* sys, int32_t n_sys, const double* E_co
 
 int qcams_run_batch(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
                     qcams_batch* batch, void* cuda_stream) {
+  clear_stale_error();
   SysSet ss;
   int rc = make_sysset(sys, n_sys, &ss);
   if (rc != QCAMS_OK) return rc;
@@ -930,29 +951,30 @@ int qcams_run_batch(const qcams_system* sys, int32_t n_sys, const qcams_integ* i
   DevBatch d = dev_batch(batch);
   k_pair_shapes<<<1, 32, 0, st>>>(ss, ctx->shapes);
   ctx->timed = false;
-  cudaError_t e = cudaEventRecord(ctx->ev[0], st);
+  cudaError_t e = record_event(ctx->ev[0], st);
   if (e == cudaSuccess)
     e = launch_integrate(ss, ctx->shapes, ip, d, integ->precision, integ->persistent,
                          integ->block, integ->blocks_per_sm, *ctx, st);
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], st);
+  if (e == cudaSuccess) e = record_event(ctx->ev[1], st);
   if (e != cudaSuccess) return QCAMS_E_CUDA;
   if (integ->fixed_step) {
-    e = cudaEventRecord(ctx->ev[2], st);
-    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], st);
+    e = record_event(ctx->ev[2], st);
+    if (e == cudaSuccess) e = record_event(ctx->ev[3], st);
     ctx->timed = e == cudaSuccess;
     return cuda_status(e);
   }
   const double sg = integ->gb_sigma > 0 ? integ->gb_sigma : 0.1 / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-  e = cudaEventRecord(ctx->ev[2], st);
+  e = record_event(ctx->ev[2], st);
   k_analyze<<<(unsigned)((batch->n + 127) / 128), 128, 0, st>>>(ss, ctx->shapes, sg, d);
   if (e == cudaSuccess) e = cudaGetLastError();
-  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[3], st);
+  if (e == cudaSuccess) e = record_event(ctx->ev[3], st);
   ctx->timed = e == cudaSuccess;
   return cuda_status(e);
 }
 
 int qcams_analyze(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
                   qcams_batch* batch, void* cuda_stream) {
+  clear_stale_error();
   SysSet ss;
   int rc = make_sysset(sys, n_sys, &ss);
   if (rc != QCAMS_OK) return rc;
@@ -972,6 +994,7 @@ int qcams_analyze(const qcams_system* sys, int32_t n_sys, const qcams_integ* int
 
 int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_t* hist_out,
                       double* xsec_out, void* cuda_stream) {
+  clear_stale_error();
   if (!batch || !cells || !hist_out || batch->n < 0) return QCAMS_E_INVALID;
   if (cells->n_cells < 1 || cells->n_groups < 0) return QCAMS_E_INVALID;
   if (cells->n_cells > kMaxCells || cells->n_groups > kMaxCells) return QCAMS_E_CAPACITY;
@@ -1057,6 +1080,94 @@ int qcams_last_run_stats(qcams_run_stats* out, void* cuda_stream) {
     if (cudaEventElapsedTime(&a, ctx->ev[0], ctx->ev[1]) == cudaSuccess) out->integrate_ms = a;
     if (cudaEventElapsedTime(&b, ctx->ev[2], ctx->ev[3]) == cudaSuccess) out->analyze_ms = b;
   }
+  return QCAMS_OK;
+}
+
+int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
+                   qcams_batch* sample, int64_t max_attempts, qcams_tune_result* results,
+                   int32_t* n_results, qcams_integ* best, void* cuda_stream) {
+  if (!results || !n_results || !best || max_attempts < 1) return QCAMS_E_INVALID;
+  SysSet ss;
+  IntegParams ip;
+  DevBatch d;
+  int rc = prepare_run(sys, n_sys, integ, sample, &ss, &ip, &d);
+  if (rc != QCAMS_OK) return rc;
+  if (integ->fixed_step || sample->n < 1) return QCAMS_E_INVALID;
+  Ctx* ctx;
+  if (ctx_get(&ctx) != cudaSuccess) return QCAMS_E_CUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int64_t n = sample->n;
+  // save the sample state: 14 double arrays, 2 int32 arrays, status
+  double* dbl[14];
+  for (int k = 0; k < 12; ++k) dbl[k] = sample->y[k];
+  dbl[12] = sample->t;
+  dbl[13] = sample->h;
+  int32_t* i32[2] = {sample->nsteps, sample->nrej};
+  const size_t bytes = (size_t)n * (14 * sizeof(double) + 2 * sizeof(int32_t) + 1);
+  unsigned char* save = nullptr;
+  if (cudaMallocAsync((void**)&save, bytes, st) != cudaSuccess) return QCAMS_E_CUDA;
+  auto copy_all = [&](bool to_save) -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    unsigned char* p = save;
+    for (int k = 0; k < 14 && e == cudaSuccess; ++k, p += n * sizeof(double))
+      e = to_save ? cudaMemcpyAsync(p, dbl[k], n * sizeof(double), cudaMemcpyDeviceToDevice, st)
+                  : cudaMemcpyAsync(dbl[k], p, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k, p += n * sizeof(int32_t))
+      e = to_save ? cudaMemcpyAsync(p, i32[k], n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st)
+                  : cudaMemcpyAsync(i32[k], p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+      e = to_save ? cudaMemcpyAsync(p, sample->status, n, cudaMemcpyDeviceToDevice, st)
+                  : cudaMemcpyAsync(sample->status, p, n, cudaMemcpyDeviceToDevice, st);
+    return e;
+  };
+  cudaError_t e = copy_all(true);
+  if (e == cudaSuccess) e = launch_shapes(ss, ctx->shapes, st);
+  IntegParams tip = ip;
+  if (tip.max_steps > max_attempts) tip.max_steps = max_attempts;
+  const bool morse = integrate_all_morse(ss);
+  const int nv = integrate_variant_count();
+  int best_v = -1;
+  double best_rate = -1.0;
+  for (int v = 0; v < nv && v < QCAMS_TUNE_MAX_VARIANTS && e == cudaSuccess; ++v) {
+    int block = 0, bps = 0;
+    integrate_variant_shape(v, &block, &bps);
+    e = copy_all(false);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], st);
+    if (e == cudaSuccess)
+      e = launch_integrate(ss, ctx->shapes, tip, d, 64, 1, block, bps, *ctx, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], st);
+    unsigned long long cnt[2] = {0, 0};
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cnt, ctx->counters, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    if (e != cudaSuccess) break;
+    qcams_tune_result& r = results[v];
+    r.block = block;
+    r.blocks_per_sm = bps;
+    r.regs = 0;
+    r.resident_blocks = 0;
+    integrate_variant_regs(v, morse, &r.regs);
+    integrate_variant_occupancy(v, morse, &r.resident_blocks);
+    r.ms = ms;
+    r.lane_steps_per_s = ms > 0.f ? (double)cnt[1] / (ms * 1e-3) : 0.0;
+    if (r.lane_steps_per_s > best_rate) {
+      best_rate = r.lane_steps_per_s;
+      best_v = v;
+    }
+    *n_results = v + 1;
+  }
+  cudaError_t e2 = copy_all(false);
+  cudaFreeAsync(save, st);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  ctx->timed = false;
+  if (e != cudaSuccess || best_v < 0) return QCAMS_E_CUDA;
+  *best = *integ;
+  best->persistent = 1;
+  best->block = results[best_v].block;
+  best->blocks_per_sm = results[best_v].blocks_per_sm;
   return QCAMS_OK;
 }
 

@@ -32,6 +32,7 @@
 
 #include "qcams_device.cuh"
 #include "qcams_internal.h"
+#include "dp5_tableau.cuh"
 
 namespace qcams {
 namespace {
@@ -80,72 +81,6 @@ __device__ __forceinline__ float signed_f(double x) {
 // Order of non-negative doubles equals the order of their bit patterns.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
-// ---------------------------------------------------------------------------
-// Dormand & Prince (1980) 5(4) tableau (1-based stage indices) and the
-// Runge-Kutta-Nystrom coefficient products derived from it at compile time.
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr double dpA(int i, int j) {
-  return (i == 2 && j == 1)   ? 1.0 / 5
-         : (i == 3 && j == 1) ? 3.0 / 40
-         : (i == 3 && j == 2) ? 9.0 / 40
-         : (i == 4 && j == 1) ? 44.0 / 45
-         : (i == 4 && j == 2) ? -56.0 / 15
-         : (i == 4 && j == 3) ? 32.0 / 9
-         : (i == 5 && j == 1) ? 19372.0 / 6561
-         : (i == 5 && j == 2) ? -25360.0 / 2187
-         : (i == 5 && j == 3) ? 64448.0 / 6561
-         : (i == 5 && j == 4) ? -212.0 / 729
-         : (i == 6 && j == 1) ? 9017.0 / 3168
-         : (i == 6 && j == 2) ? -355.0 / 33
-         : (i == 6 && j == 3) ? 46732.0 / 5247
-         : (i == 6 && j == 4) ? 49.0 / 176
-         : (i == 6 && j == 5) ? -5103.0 / 18656
-         : (i == 7 && j == 1) ? 35.0 / 384
-         : (i == 7 && j == 3) ? 500.0 / 1113
-         : (i == 7 && j == 4) ? 125.0 / 192
-         : (i == 7 && j == 5) ? -2187.0 / 6784
-         : (i == 7 && j == 6) ? 11.0 / 84
-                              : 0.0;
-}
-__host__ __device__ constexpr double dpC(int i) {
-  return i == 2 ? 1.0 / 5 : i == 3 ? 3.0 / 10 : i == 4 ? 4.0 / 5 : i == 5 ? 8.0 / 9
-         : (i >= 6) ? 1.0 : 0.0;
-}
-// 5th-order weights b = 7th row of A (FSAL); error weights e = b - b*.
-__host__ __device__ constexpr double dpB(int j) { return dpA(7, j); }
-__host__ __device__ constexpr double dpE(int j) {
-  return j == 1 ? 71.0 / 57600 : j == 3 ? -71.0 / 16695 : j == 4 ? 71.0 / 1920
-         : j == 5 ? -17253.0 / 339200 : j == 6 ? 22.0 / 525 : j == 7 ? -1.0 / 40 : 0.0;
-}
-__host__ __device__ constexpr double dpA2(int s, int q) {
-  double acc = 0.0;
-  for (int j = 1; j <= 7; ++j) acc += dpA(s, j) * dpA(j, q);
-  return acc;
-}
-__host__ __device__ constexpr double dpEA(int q) {
-  double acc = 0.0;
-  for (int i = 1; i <= 7; ++i) acc += dpE(i) * dpA(i, q);
-  return acc;
-}
-
-struct RknTab {
-  double a2[8][8];  // (A^2)_{s,q}, s,q 1-based
-  double c[8];
-  double b[8];
-  double e[8];
-  double ea[8];     // (e^T A)_q
-};
-__host__ __device__ constexpr RknTab make_rkn_tab() {
-  RknTab t{};
-  for (int s = 1; s <= 7; ++s) {
-    t.c[s] = dpC(s);
-    t.b[s] = dpB(s);
-    t.e[s] = dpE(s);
-    t.ea[s] = dpEA(s);
-    for (int q = 1; q <= 7; ++q) t.a2[s][q] = dpA2(s, q);
-  }
-  return t;
-}
 // Coefficients in the constant bank: a DFMA takes a constant-bank operand at
 // full rate, so indexing this table with compile-time indices costs nothing.
 __constant__ RknTab kT = make_rkn_tab();
@@ -469,8 +404,8 @@ __device__ __forceinline__ void load_exp_table(double* sT) {
 }
 
 // One thread per trajectory.
-template <bool MORSE>
-__global__ void __launch_bounds__(128) k_integrate_plain(SysSet sys, const DevShape* shapes,
+template <bool MORSE, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_integrate_plain(SysSet sys, const DevShape* shapes,
                                                          IntegParams ip, DevBatch B,
                                                          unsigned long long* counters) {
   __shared__ double sT[256];
@@ -489,8 +424,8 @@ __global__ void __launch_bounds__(128) k_integrate_plain(SysSet sys, const DevSh
 
 // Persistent refill-queue launch: each warp pops trajectory indices for all
 // of its idle lanes with one atomicAdd (ballot + popc + shuffle).
-template <bool MORSE>
-__global__ void __launch_bounds__(128) k_integrate_persistent(SysSet sys, const DevShape* shapes,
+template <bool MORSE, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB) k_integrate_persistent(SysSet sys, const DevShape* shapes,
                                                               IntegParams ip, DevBatch B,
                                                               unsigned long long* counters) {
   __shared__ double sT[256];
@@ -600,40 +535,63 @@ bool all_morse(const SysSet& s) {
   return true;
 }
 
-template <bool MORSE>
-cudaError_t launch_fp64(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
-                        const DevBatch& b, int persistent, int block, int blocks_per_sm, Ctx& ctx,
-                        cudaStream_t st) {
+// Launch-shape variants: threads per block and the resident blocks per SM
+// each kernel is compiled for (__launch_bounds__ minimum, which caps the
+// registers per thread).  At ~190 registers, 64-thread blocks fit 5 per SM
+// (10 warps) where 128-thread blocks fit 2 (8 warps); the autotuner measures.
+struct Variant {
+  int block, minb;
+};
+constexpr Variant kVariants[] = {{128, 1}, {64, 1}, {128, 3}, {64, 6}, {64, 7}, {256, 1}};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
+int find_variant(int block, int minb) {
   if (block <= 0) block = 128;
-  if (block > 128) block = 128;
-  block = (block / 32) * 32;
-  if (block == 0) block = 32;
-  if (ip.fixed_step) {
-    unsigned grid = (unsigned)((b.n + block - 1) / block);
-    k_integrate_fixed<MORSE><<<grid, block, 0, st>>>(sys, ip, b, ctx.counters);
-    return cudaGetLastError();
-  }
+  if (minb <= 0) minb = 1;
+  for (int v = 0; v < kNumVariants; ++v)
+    if (kVariants[v].block == block && kVariants[v].minb == minb) return v;
+  return -1;
+}
+
+template <bool MORSE, int BLOCK, int MINB>
+cudaError_t launch_shape(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
+                         const DevBatch& b, int persistent, Ctx& ctx, cudaStream_t st,
+                         int* blocks_per_sm_out) {
   if (persistent) {
     cudaError_t e = cudaMemsetAsync(ctx.counters + 2, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    int per_sm = blocks_per_sm;
-    if (per_sm <= 0) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_integrate_persistent<MORSE>,
-                                                        block, 0);
-      if (e != cudaSuccess) return e;
-      if (per_sm < 1) per_sm = 1;
-    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_integrate_persistent<MORSE, BLOCK, MINB>, BLOCK, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (blocks_per_sm_out) *blocks_per_sm_out = per_sm;
     long long grid = (long long)per_sm * ctx.sm_count;
-    long long need = (b.n + block - 1) / block;
+    const long long need = (b.n + BLOCK - 1) / BLOCK;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_integrate_persistent<MORSE><<<(unsigned)grid, block, 0, st>>>(sys, shapes, ip, b,
-                                                                    ctx.counters);
+    k_integrate_persistent<MORSE, BLOCK, MINB><<<(unsigned)grid, BLOCK, 0, st>>>(
+        sys, shapes, ip, b, ctx.counters);
     return cudaGetLastError();
   }
-  unsigned grid = (unsigned)((b.n + block - 1) / block);
-  k_integrate_plain<MORSE><<<grid, block, 0, st>>>(sys, shapes, ip, b, ctx.counters);
+  const unsigned grid = (unsigned)((b.n + BLOCK - 1) / BLOCK);
+  k_integrate_plain<MORSE, BLOCK, MINB><<<grid, BLOCK, 0, st>>>(sys, shapes, ip, b, ctx.counters);
   return cudaGetLastError();
+}
+
+template <bool MORSE>
+cudaError_t launch_variant(int v, const SysSet& sys, const DevShape* shapes,
+                           const IntegParams& ip, const DevBatch& b, int persistent, Ctx& ctx,
+                           cudaStream_t st, int* bps) {
+  switch (v) {
+    case 0: return launch_shape<MORSE, 128, 1>(sys, shapes, ip, b, persistent, ctx, st, bps);
+    case 1: return launch_shape<MORSE, 64, 1>(sys, shapes, ip, b, persistent, ctx, st, bps);
+    case 2: return launch_shape<MORSE, 128, 3>(sys, shapes, ip, b, persistent, ctx, st, bps);
+    case 3: return launch_shape<MORSE, 64, 6>(sys, shapes, ip, b, persistent, ctx, st, bps);
+    case 4: return launch_shape<MORSE, 64, 7>(sys, shapes, ip, b, persistent, ctx, st, bps);
+    case 5: return launch_shape<MORSE, 256, 1>(sys, shapes, ip, b, persistent, ctx, st, bps);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -650,10 +608,68 @@ cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const In
   if (b.n == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(ctx.counters, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  (void)precision;
-  if (all_morse(sys))
-    return launch_fp64<true>(sys, shapes, ip, b, persistent, block, blocks_per_sm, ctx, st);
-  return launch_fp64<false>(sys, shapes, ip, b, persistent, block, blocks_per_sm, ctx, st);
+  const bool morse = all_morse(sys);
+  if (precision == 32) return launch_integrate32(sys, shapes, ip, b, persistent, ctx, st, morse);
+  if (ip.fixed_step) {
+    const unsigned grid = (unsigned)((b.n + 127) / 128);
+    if (morse) k_integrate_fixed<true><<<grid, 128, 0, st>>>(sys, ip, b, ctx.counters);
+    else k_integrate_fixed<false><<<grid, 128, 0, st>>>(sys, ip, b, ctx.counters);
+    return cudaGetLastError();
+  }
+  const int v = find_variant(block, blocks_per_sm);
+  if (v < 0) return cudaErrorInvalidValue;
+  return morse ? launch_variant<true>(v, sys, shapes, ip, b, persistent, ctx, st, nullptr)
+               : launch_variant<false>(v, sys, shapes, ip, b, persistent, ctx, st, nullptr);
 }
+
+int integrate_variant_count() { return kNumVariants; }
+
+void integrate_variant_shape(int v, int* block, int* minb) {
+  *block = kVariants[v].block;
+  *minb = kVariants[v].minb;
+}
+
+bool integrate_shape_supported(int block, int blocks_per_sm) {
+  return find_variant(block, blocks_per_sm) >= 0;
+}
+
+cudaError_t integrate_variant_regs(int v, bool morse, int* regs) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaErrorInvalidValue;
+#define QCAMS_REGS(M, B, N) e = cudaFuncGetAttributes(&a, k_integrate_persistent<M, B, N>)
+  switch (v) {
+    case 0: if (morse) QCAMS_REGS(true, 128, 1); else QCAMS_REGS(false, 128, 1); break;
+    case 1: if (morse) QCAMS_REGS(true, 64, 1); else QCAMS_REGS(false, 64, 1); break;
+    case 2: if (morse) QCAMS_REGS(true, 128, 3); else QCAMS_REGS(false, 128, 3); break;
+    case 3: if (morse) QCAMS_REGS(true, 64, 6); else QCAMS_REGS(false, 64, 6); break;
+    case 4: if (morse) QCAMS_REGS(true, 64, 7); else QCAMS_REGS(false, 64, 7); break;
+    case 5: if (morse) QCAMS_REGS(true, 256, 1); else QCAMS_REGS(false, 256, 1); break;
+    default: break;
+  }
+#undef QCAMS_REGS
+  if (e == cudaSuccess) *regs = a.numRegs;
+  return e;
+}
+
+cudaError_t integrate_variant_occupancy(int v, bool morse, int* blocks_per_sm) {
+  const SysSet* none = nullptr;
+  (void)none;
+  cudaError_t e = cudaErrorInvalidValue;
+#define QCAMS_OCC(M, B, N) \
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_integrate_persistent<M, B, N>, B, 0)
+  switch (v) {
+    case 0: if (morse) QCAMS_OCC(true, 128, 1); else QCAMS_OCC(false, 128, 1); break;
+    case 1: if (morse) QCAMS_OCC(true, 64, 1); else QCAMS_OCC(false, 64, 1); break;
+    case 2: if (morse) QCAMS_OCC(true, 128, 3); else QCAMS_OCC(false, 128, 3); break;
+    case 3: if (morse) QCAMS_OCC(true, 64, 6); else QCAMS_OCC(false, 64, 6); break;
+    case 4: if (morse) QCAMS_OCC(true, 64, 7); else QCAMS_OCC(false, 64, 7); break;
+    case 5: if (morse) QCAMS_OCC(true, 256, 1); else QCAMS_OCC(false, 256, 1); break;
+    default: break;
+  }
+#undef QCAMS_OCC
+  return e;
+}
+
+bool integrate_all_morse(const SysSet& sys) { return all_morse(sys); }
 
 }  // namespace qcams

@@ -46,4 +46,17 @@ cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const In
                              const DevBatch& b, int precision, int persistent, int block,
                              int blocks_per_sm, Ctx& ctx, cudaStream_t st);
 
+// FP32 integrator with compensated state updates (integrate32.cu).
+cudaError_t launch_integrate32(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
+                               const DevBatch& b, int persistent, Ctx& ctx, cudaStream_t st,
+                               bool all_morse);
+
+// Launch-shape variants of the integrator (integrate.cu), for the autotuner.
+int integrate_variant_count();
+void integrate_variant_shape(int v, int* block, int* blocks_per_sm);
+bool integrate_shape_supported(int block, int blocks_per_sm);
+cudaError_t integrate_variant_regs(int v, bool morse, int* regs);
+cudaError_t integrate_variant_occupancy(int v, bool morse, int* blocks_per_sm);
+bool integrate_all_morse(const SysSet& sys);
+
 }  // namespace qcams

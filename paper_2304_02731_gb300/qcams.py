@@ -36,7 +36,7 @@ GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
 EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
            "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
-           "qcams_debug_exp"]
+           "qcams_debug_exp", "qcams_autotune"]
 
 
 class QcamsError(RuntimeError):
@@ -82,6 +82,12 @@ class RunStats(C.Structure):
                 ("analyze_ms", C.c_double)]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("regs", C.c_int32),
+                ("resident_blocks", C.c_int32), ("ms", C.c_double),
+                ("lane_steps_per_s", C.c_double)]
+
+
 class Cells(C.Structure):
     _fields_ = [("n_cells", C.c_int32), ("n_groups", C.c_int32), ("b", C.c_void_p),
                 ("w", C.c_void_p), ("group", C.c_void_p), ("weighted", C.c_int32),
@@ -119,6 +125,8 @@ def lib():
                 "qcams_shutdown": (C.c_int, []),
                 "qcams_run_batch_noalloc": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
                 "qcams_debug_exp": (C.c_int, [V, V, V, I64, V]),
+                "qcams_autotune": (C.c_int, [P(System), I32, P(Integ), P(CBatch), I64,
+                                             P(TuneResult), P(I32), P(Integ), V]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -254,10 +262,14 @@ class Batch:
 
 
 def _dptr(x, dtype, device):
+    """(device tensor, staged) — staged is True when a copy was made."""
+    if isinstance(x, torch.Tensor) and x.device == device and x.dtype == dtype \
+            and x.is_contiguous():
+        return x, False
     t = torch.as_tensor(x, dtype=dtype)
     if t.device != device:
         t = t.to(device, non_blocking=True)
-    return t.contiguous()
+    return t.contiguous(), True
 
 
 # ---------------------------------------------------------------------------
@@ -286,16 +298,16 @@ def init_states(systems, batch: Batch, E, b, v, j, R0: float, seed: int, id_offs
     """qcams_init_states on `batch` (inputs may be host or device arrays)."""
     arr = systems_array(systems)
     dev = batch.device
-    tE = _dptr(E, torch.float64, dev)
-    tb = _dptr(b, torch.float64, dev)
-    tv = _dptr(v, torch.int32, dev)
-    tj = _dptr(j, torch.int32, dev)
-    keep = [tE, tb, tv, tj]
+    staged = [_dptr(E, torch.float64, dev), _dptr(b, torch.float64, dev),
+              _dptr(v, torch.int32, dev), _dptr(j, torch.int32, dev)]
+    tE, tb, tv, tj = [t for t, _ in staged]
     uptr = None
     if u_in is not None:
-        tu = _dptr(u_in, torch.float64, dev).reshape(4, batch.n)
-        keep.append(tu)
+        tu, cp = _dptr(u_in, torch.float64, dev)
+        tu = tu.reshape(4, batch.n)
+        staged.append((tu, cp))
         uptr = (C.c_void_p * 4)(*[tu[k].data_ptr() for k in range(4)])
+    keep = [t for t, cp in staged if cp]
     rc = lib().qcams_init_states(arr, len(systems), tE.data_ptr(), tb.data_ptr(), tv.data_ptr(),
                                  tj.data_ptr(), float(R0), int(seed), int(id_offset), uptr,
                                  C.byref(batch.c), _stream(stream))
@@ -372,6 +384,22 @@ def fma_peak(precision: int = 64, stream=None) -> float:
     f = C.c_double()
     _check(lib().qcams_fma_peak(int(precision), C.byref(f), _stream(stream)), "qcams_fma_peak")
     return f.value
+
+
+def autotune(systems, sample: Batch, integ: Integ, max_attempts: int = 1500, stream=None):
+    """qcams_autotune: measure every launch shape on an initialised sample
+    batch; returns (best Integ, list of per-variant result dicts)."""
+    arr = systems_array(systems)
+    res = (TuneResult * 16)()
+    nres = C.c_int32()
+    best = Integ()
+    _check(lib().qcams_autotune(arr, len(systems), C.byref(integ), C.byref(sample.c),
+                                int(max_attempts), res, C.byref(nres), C.byref(best),
+                                _stream(stream)), "qcams_autotune")
+    out = [dict(block=r.block, blocks_per_sm=r.blocks_per_sm, regs=r.regs,
+                resident_blocks=r.resident_blocks, ms=r.ms, lane_steps_per_s=r.lane_steps_per_s)
+           for r in res[:nres.value]]
+    return best, out
 
 
 def debug_exp(x: torch.Tensor, stream=None):

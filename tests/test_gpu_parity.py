@@ -284,3 +284,106 @@ def test_table_exp_matches_cuda_exp(Q):
     lo = torch.tensor([-701.0, -800.0, -1e6], dtype=torch.float64, device="cuda")
     m2, r2 = Q.debug_exp(lo)
     assert torch.all(m2 > 0) and torch.all(m2 < 1e-303)
+
+
+def test_autotune_restores_sample_and_shapes_agree(Q):
+    """The autotuner leaves its sample untouched, and every launch shape
+    integrates each lane identically (bit-for-bit)."""
+    import torch
+    wl = W.sweep_h2_ca(per_cell=4, n_E=4, n_b=6)
+    integ = Q.make_integ(**wl.integ, persistent=True)
+    batch = Q.Batch.empty(wl.n, "cuda", sys_id=wl.sys_id, cell=wl.cell)
+    Q.init_states(wl.systems, batch, wl.E, wl.b, wl.v, wl.j, wl.R0, wl.seed)
+    torch.cuda.synchronize()
+    before = batch.host()
+    best, table = Q.autotune(wl.systems, batch, integ, max_attempts=300)
+    after = batch.host()
+    assert len(table) == 6 and all(r["lane_steps_per_s"] > 0 for r in table)
+    for k in ["y", "t", "h", "status", "nsteps", "nrej"]:
+        assert np.array_equal(before[k], after[k]), k
+    outs = []
+    for block, bps in [(128, 1), (64, 1), (64, 6), (256, 1), (best.block, best.blocks_per_sm)]:
+        it = Q.make_integ(**wl.integ, persistent=True, block=block, blocks_per_sm=bps)
+        b2, hist, _, _ = Q.run_workload(wl, it, finalize=False)
+        torch.cuda.synchronize()
+        outs.append(b2.host())
+    for o in outs[1:]:
+        for k in ["y", "t", "status", "cls", "nsteps", "nrej", "vprime"]:
+            assert np.array_equal(o[k], outs[0][k]), k
+
+
+def test_graph_replay_matches_eager(Q):
+    """init + run + reduce captured in a CUDA graph and replayed gives the
+    same per-lane results and histograms as eager calls."""
+    import torch
+    wl = W.sweep_h2_ca(per_cell=4, n_E=3, n_b=5)
+    integ = Q.make_integ(**wl.integ, persistent=True)
+    dev = torch.device("cuda")
+    batch = Q.Batch.empty(wl.n, dev, sys_id=wl.sys_id, cell=wl.cell)
+    E, b = torch.as_tensor(wl.E, device=dev), torch.as_tensor(wl.b, device=dev)
+    v, j = torch.as_tensor(wl.v, device=dev), torch.as_tensor(wl.j, device=dev)
+    hist = torch.empty(wl.n_cells * Q.H_STRIDE, dtype=torch.int64, device=dev)
+
+    def step():
+        Q.init_states(wl.systems, batch, E, b, v, j, wl.R0, wl.seed)
+        Q.run_batch(wl.systems, batch, integ)
+        Q.reduce_xsec(batch, wl.n_cells, hist_out=hist, finalize=False)
+
+    step()
+    torch.cuda.synchronize()
+    eager, h_eager = batch.host(), hist.cpu().numpy()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    batch.y.zero_()
+    hist.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    rep = batch.host()
+    for k in ["y", "t", "status", "cls", "nsteps", "vt", "gbw"]:
+        assert np.array_equal(rep[k], eager[k]), k
+    assert np.array_equal(hist.cpu().numpy(), h_eager)
+
+
+def test_fp32_kahan_integrator_against_fp64(Q, oracle):
+    """FP32 integrator with compensated updates (tolerances 1e-6 / 1e-8) on a
+    sweep sample, against the FP64 path on the same lanes: energy drift,
+    class agreement for lanes that reached a product, cross sections within
+    3 combined standard errors.  The plain study (closed channels) must stay
+    all-quench."""
+    import torch
+    wl = W.sweep_h2_ca(per_cell=24)
+    wl = wl.take(W.stratified(wl, 24))
+    res = {}
+    for prec, kw in [(64, W.INTEG_FP64), (32, W.INTEG_FP32)]:
+        integ = Q.make_integ(**kw, persistent=True, precision=prec)
+        b, hist, cells, groups = Q.run_workload(wl, integ)
+        torch.cuda.synchronize()
+        res[prec] = (b.host(), groups)
+    h64, g64 = res[64]
+    h32, g32 = res[32]
+    assert np.all(np.isin(h32["status"], [2, 3]))
+    sep = h32["status"] == 2
+    rel32 = np.abs(h32["dE"][sep]) / np.maximum(np.abs(h32["E0"][sep]), wl.E[sep])
+    done = (h32["status"] == 2) & (h64["status"] == 2)
+    agree = np.mean(h32["cls"][done] == h64["cls"][done])
+    worst = 0.0
+    for g in range(wl.n_groups):
+        for k in range(4):
+            se = math.hypot(g64[g, k, 1], g32[g, k, 1])
+            d = abs(g64[g, k, 0] - g32[g, k, 0])
+            if se > 0:
+                worst = max(worst, d / se)
+            assert d <= 3.0 * se + 1e-9, (g, k, g64[g, k], g32[g, k])
+    print(f"\nFP32+Kahan: median |dE/E| {np.median(rel32):.2e}, 99% {np.quantile(rel32, .99):.2e}; "
+          f"class agreement with FP64 on {done.sum()} product lanes {agree:.4f}; "
+          f"max sigma deviation {worst:.2f} SE; steps/lane FP32 {h32['nsteps'].mean():.0f} "
+          f"vs FP64 {h64['nsteps'].mean():.0f}")
+    assert np.median(rel32) < 1e-5
+    assert agree >= 0.95
+    wl0 = W.plain_h2_ca(per_b=40)
+    b0, _, _, g0 = Q.run_workload(wl0, Q.make_integ(**W.INTEG_FP32, persistent=True,
+                                                     precision=32))
+    torch.cuda.synchronize()
+    h0 = b0.host()
+    assert np.all(h0["cls"][h0["status"] == 2] == 0)
