@@ -398,6 +398,7 @@ def run_ours(args):
         "gpu_launches": 8 * args.steps,
         "clocks": clock_info,
         "outcomes": {"cls_counts_Q_RAC_RBC_D_AMBIG_FAIL": cls_counts,
+                     "sigma_entries": "Q, R_AC, R_BC, D, AMBIG, FAIL, R_AC+R_BC",
                      "sigma_first_group": groups[0, :, 0].tolist() if groups is not None and
                      len(groups) else None},
     }

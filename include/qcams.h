@@ -291,6 +291,7 @@ int qcams_analyze(const qcams_system* sys, int32_t n_sys, const qcams_integ* int
 #define QCAMS_H_W 1160
 #define QCAMS_H_W2 1168
 #define QCAMS_H_STRIDE 1176
+#define QCAMS_XSEC_ENTRIES 7
 
 typedef struct {
   int32_t n_cells;      /* cells referenced by batch->cell, <= 65536 */
@@ -309,13 +310,15 @@ typedef struct {
  * into hist_out (device, n_cells * QCAMS_H_STRIDE int64, zeroed by this
  * call).  Lanes with a cell outside [0, n_cells) are ignored.
  * If xsec_out (host) is non-NULL the call synchronises the stream, copies
- * the histograms back and writes, in doubles,
- *   per cell c, class k:  xsec_out[12 c + 2 k] = P_k = N_k / N,
- *                         xsec_out[12 c + 2 k + 1] = delta_k
+ * the histograms back and writes, in doubles, with E = QCAMS_XSEC_ENTRIES
+ * entries per cell and per group (k = 0..5 the classes, k = 6 the reactive
+ * total R_AC + R_BC):
+ *   per cell c, entry k:  xsec_out[2E c + 2 k] = P_k = N_k / N,
+ *                         xsec_out[2E c + 2 k + 1] = delta_k
  *                         = sqrt(N_k)/N sqrt((N - N_k)/N)   (Eq. 16),
  *     with N the lanes of classes Q, R_AC, R_BC, D, AMBIG (failures are
  *     excluded); weighted mode: P_k = sum(isw 1_k)/N and its sample error;
- *   then per group g: xsec_out[12 n_cells + 12 g + 2 k] = sigma_k
+ *   then per group g: xsec_out[2E n_cells + 2E g + 2 k] = sigma_k
  *                         = 2 pi sum_{c in g} w_c b_c P_k(c),
  *     [.. + 1] = 2 pi sqrt(sum (w_c b_c delta_k(c))^2).
  * (Eq. 18 prints the prefactor 8 pi^2; the 8 pi^2 of the angular measure
@@ -374,6 +377,98 @@ typedef struct {
 int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
                    qcams_batch* sample, int64_t max_attempts, qcams_tune_result* results,
                    int32_t* n_results, qcams_integ* best, void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Learned importance-sampling proposal (the outcome study's extension:    */
+/* the sampled trajectories are still integrated exactly; the proposal     */
+/* only reweights where in (b^2, cos theta, phi, eta, chi) they are drawn). */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * MLP 8 -> 64 -> 64 -> 64 -> 4 with SiLU (z sigmoid(z)) hidden activations
+ * and softmax outputs over (Q, R_AC, R_BC, D).  Inputs, in order: E_col, b,
+ * v, j, theta, phi, chi, eta, standardised with x_mean / x_std.  FP32 master
+ * parameters, layout (row-major): W1[64][8] b1[64] W2[64][64] b2[64]
+ * W3[64][64] b3[64] W4[4][64] b4[4].  Matrix products run on the tensor
+ * cores in BF16 (weights and activations rounded to BF16) with FP32
+ * accumulation; biases, activations, softmax and Adam are FP32.
+ * All pointers are caller-owned device arrays of QCAMS_MLP_NPARAMS elements.
+ */
+#define QCAMS_MLP_NPARAMS 9156
+typedef struct {
+  float* params;        /* FP32 master parameters */
+  float* adam_m;        /* Adam first moments */
+  float* adam_v;        /* Adam second moments */
+  float* grad;          /* gradient of the last train / grad call */
+  uint16_t* params_bf16;/* BF16 copy used by the tensor-core kernels */
+  float x_mean[8];      /* input standardisation (host values) */
+  float x_std[8];
+  int64_t step;         /* Adam steps taken */
+} qcams_mlp;
+
+/* Parameters W ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from Philox4x32-10
+ * (key = seed, counter words (index, 0, 3, 0), first output word), biases 0,
+ * moments 0, step 0, standardisation = identity.  Asynchronous. */
+int qcams_mlp_init(qcams_mlp* m, uint64_t seed, void* cuda_stream);
+/* Refresh params_bf16 from params (after the caller writes params). */
+int qcams_mlp_sync(const qcams_mlp* m, void* cuda_stream);
+/* Network inputs of initialised lanes: x[i] = (E_col, b, v, j, theta, phi,
+ * chi, eta) from the lane inputs and the uniforms batch->u written by
+ * qcams_init_states (theta = acos(2 u0 - 1), phi = 2 pi u1, eta = 2 pi u2,
+ * chi = u3).  x: device float [n][8].  Asynchronous. */
+int qcams_mlp_features(const qcams_batch* batch, const double* E_col, const double* b,
+                       const int32_t* v, const int32_t* j, float* x, void* cuda_stream);
+/* Set x_mean / x_std to the mean and standard deviation of x[n][8]
+ * (device); synchronises. */
+int qcams_mlp_fit_standardizer(qcams_mlp* m, const float* x, int64_t n, void* cuda_stream);
+/* Softmax cross-entropy summed over the n samples and divided by n, with
+ * targets the outcome classes cls[n] as qcams_run_batch writes them (device
+ * uint8: Q, R_AC, R_BC, D = 0..3; AMBIG and FAIL samples contribute
+ * nothing), and its gradient into m->grad; *loss_out (device float,
+ * optional) receives the loss.  Asynchronous. */
+int qcams_mlp_grad(const qcams_mlp* m, const float* x, const uint8_t* cls, int64_t n,
+                   float* loss_out, void* cuda_stream);
+/* qcams_mlp_grad followed by one Adam step (beta1 0.9, beta2 0.999,
+ * eps 1e-8, bias-corrected) with learning rate lr; increments m->step. */
+int qcams_mlp_train_step(qcams_mlp* m, const float* x, const uint8_t* cls, int64_t n,
+                         float lr, float* loss_out, void* cuda_stream);
+/* Class probabilities probs[n][4] (device float) for inputs x[n][8]. */
+int qcams_mlp_infer(const qcams_mlp* m, const float* x, int64_t n, float* probs,
+                    void* cuda_stream);
+
+/*
+ * Proposal over one (E_col, v, j): an n_b2 x n_cth x n_phi x n_eta x n_chi
+ * grid of equal-measure cells in (b^2 in [0, b2_max], cos theta, phi, eta,
+ * chi); cell index ((((i_b2 n_cth + i_cth) n_phi + i_phi) n_eta + i_eta)
+ * n_chi + i_chi).  q_c = alpha / N + (1 - alpha) g_c / sum g with
+ * g_c = sqrt(eps + p_R(centre of c)), p_R = P(R_AC) + P(R_BC) from the MLP
+ * (defensive mixture: q_c >= alpha / N, so every weight is <= 1 / alpha).
+ * q (device double [N]); qfix (device int64 [N]) = round(q 2^40) and
+ * cdf (device int64 [N]) its inclusive prefix sums: sampling uses the exact
+ * integer distribution qfix / cdf[N-1].  N <= 2^22.  Asynchronous.
+ */
+typedef struct {
+  double E_col;
+  int32_t v, j;
+  int32_t n_b2, n_cth, n_phi, n_eta, n_chi, pad;
+  double b2_max, eps, alpha;
+} qcams_proposal_spec;
+int qcams_build_proposal(const qcams_mlp* m, const qcams_proposal_spec* spec, double* q,
+                         int64_t* qfix, int64_t* cdf, void* cuda_stream);
+/*
+ * Draw n lanes from the proposal: for lane i, Philox4x32-10 with key = seed
+ * and counter words (id_lo, id_hi, 1, 0) then (id_lo, id_hi, 2, 0), id =
+ * id_offset + i, gives u_0..u_7 = (word + 1/2) 2^-32; cell c = first index
+ * with cdf[c] > floor(u_0 cdf[N-1]) (computed exactly in integers); inside c: b^2 = b2_max (i_b2 + u_1)/n_b2, cos theta
+ * = 2 (i_cth + u_2)/n_cth - 1, phi / 2 pi = (i_phi + u_3)/n_phi, eta / 2 pi
+ * = (i_eta + u_4)/n_eta, chi = (i_chi + u_5)/n_chi.  Outputs (device):
+ * b[n], u_out[0..3][n] = the uniforms qcams_init_states takes as u_in,
+ * w[n] = (cdf[N-1] / N) / qfix[c] (the likelihood ratio), cell[n].
+ */
+int qcams_sample_proposal(const qcams_proposal_spec* spec, const int64_t* qfix,
+                          const int64_t* cdf, int64_t n, uint64_t seed, uint64_t id_offset,
+                          double* b, double* const* u_out, double* w, int32_t* cell,
+                          void* cuda_stream);
 
 /* ---------------------------------------------------------------------- */
 /* Measurement and housekeeping.                                           */

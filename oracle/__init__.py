@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qcams_oracle.cpp")
+_SRC_IS = os.path.join(_HERE, "qcams_oracle_is.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -79,12 +80,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle with g++ (no FMA contraction) into oracle/_build."""
     with _lock:
         os.makedirs(_BUILD, exist_ok=True)
-        if (not force and os.path.exists(_LIB_PATH)
-                and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_IS))
+        if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
             return _LIB_PATH
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-shared",
-               "-fPIC", _SRC, "-o", tmp]
+               "-fPIC", _SRC, _SRC_IS, "-o", tmp]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
@@ -120,6 +121,18 @@ def lib():
                                       C.c_void_p]),
             "oracle_reduce": (None, [C.c_int64, _I32, _I32, _I32, _D, _D, _I32, C.c_int32, _I64]),
             "oracle_xsec": (None, [_I64, C.c_int32, _D, _D, _I32, C.c_int32, C.c_int32, _D]),
+            "oracle_mlp_num_params": (C.c_int, []),
+            "oracle_mlp_forward": (None, [_D, _D, C.c_int64, _D]),
+            "oracle_mlp_loss_grad": (C.c_double, [_D, _D, _I32, C.c_int64, _D]),
+            "oracle_adam_step": (None, [_D, _D, _D, _D, C.c_int64, C.c_int64, C.c_double,
+                                        C.c_double, C.c_double, C.c_double]),
+            "oracle_proposal": (None, [_D, _D, C.c_int64, C.c_double, C.c_double, _D]),
+            "oracle_proposal_cdf": (None, [_D, C.c_int64, _I64, _I64]),
+            "oracle_sample_proposal": (None, [_I32, C.c_double, _I64, _I64, C.c_int64, C.c_int64,
+                                              C.c_uint64, C.c_uint64, _D, _D, _D, _I32]),
+            "oracle_is_mean": (None, [_D, _D, C.c_int64, _D, _D]),
+            "oracle_proposal_grid": (None, [_I32, C.c_double, C.c_double, C.c_int32, C.c_int32,
+                                            _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -364,12 +377,12 @@ def reduce(cls, vt, jt, gbw, cell, n_cells, isw=None):
 def xsec(hist, cell_b, cell_w, group, n_groups, weighted=False):
     hist = np.ascontiguousarray(hist, np.int64)
     n_cells = hist.shape[0]
-    out = np.zeros(12 * n_cells + 12 * n_groups)
+    out = np.zeros(14 * n_cells + 14 * n_groups)
     lib().oracle_xsec(hist.ctypes.data_as(_I64), n_cells, _d(_arr(cell_b, np.float64)),
                       _d(_arr(cell_w, np.float64)), _i32(_arr(group, np.int32)), int(n_groups),
                       int(bool(weighted)), _d(out))
-    cells = out[:12 * n_cells].reshape(n_cells, 6, 2)
-    groups = out[12 * n_cells:].reshape(n_groups, 6, 2)
+    cells = out[:14 * n_cells].reshape(n_cells, 7, 2)
+    groups = out[14 * n_cells:].reshape(n_groups, 7, 2)
     return cells, groups
 
 
@@ -378,3 +391,79 @@ def run_lanes(systems, sys_id, Ecol, b, v, j, R0, seed, integ: OInteg, id_offset
     st = init(systems, sys_id, Ecol, b, v, j, R0, seed, id_offset, u_in)
     res = run_adaptive(systems, sys_id, integ, st["y"], st["t_scale"], st["E0"], st["status"])
     return st, res
+
+
+# ---------------------------------------------------------------------------
+# learned proposal (qcams_oracle_is.cpp)
+# ---------------------------------------------------------------------------
+MLP_NPARAMS = 9156
+
+
+def mlp_forward(params, x):
+    params = _arr(params, np.float64)
+    x = _arr(x, np.float64).reshape(-1, 8)
+    out = np.zeros((x.shape[0], 4))
+    lib().oracle_mlp_forward(_d(params), _d(x), x.shape[0], _d(out))
+    return out
+
+
+def mlp_loss_grad(params, x, labels):
+    params = _arr(params, np.float64)
+    x = _arr(x, np.float64).reshape(-1, 8)
+    lab = _arr(labels, np.int32)
+    g = np.zeros(MLP_NPARAMS)
+    loss = lib().oracle_mlp_loss_grad(_d(params), _d(x), _i32(lab), x.shape[0], _d(g))
+    return loss, g
+
+
+def adam_step(params, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    params, m, v = (np.array(a, np.float64) for a in (params, m, v))
+    g = _arr(grad, np.float64)
+    lib().oracle_adam_step(_d(params), _d(m), _d(v), _d(g), params.size, int(t), float(lr),
+                           float(beta1), float(beta2), float(eps))
+    return params, m, v
+
+
+def proposal(params, x_cells, eps, alpha):
+    params = _arr(params, np.float64)
+    x = _arr(x_cells, np.float64).reshape(-1, 8)
+    q = np.zeros(x.shape[0])
+    lib().oracle_proposal(_d(params), _d(x), x.shape[0], float(eps), float(alpha), _d(q))
+    return q
+
+
+def proposal_cdf(q):
+    q = _arr(q, np.float64)
+    qfix = np.zeros(q.size, np.int64)
+    cdf = np.zeros(q.size, np.int64)
+    lib().oracle_proposal_cdf(_d(q), q.size, qfix.ctypes.data_as(_I64), cdf.ctypes.data_as(_I64))
+    return qfix, cdf
+
+
+def sample_proposal(dims, b2_max, qfix, cdf, n, seed, id_offset=0):
+    dims = _arr(dims, np.int32)
+    qfix = _arr(qfix, np.int64)
+    cdf = _arr(cdf, np.int64)
+    b, u, w = np.zeros(n), np.zeros((n, 4)), np.zeros(n)
+    cell = np.zeros(n, np.int32)
+    lib().oracle_sample_proposal(_i32(dims), float(b2_max), qfix.ctypes.data_as(_I64),
+                                 cdf.ctypes.data_as(_I64), qfix.size, int(n), int(seed),
+                                 int(id_offset), _d(b), _d(u), _d(w), _i32(cell))
+    return b, u, w, cell
+
+
+def is_mean(w, f):
+    w = _arr(w, np.float64)
+    f = _arr(f, np.float64)
+    mean, se = C.c_double(), C.c_double()
+    lib().oracle_is_mean(_d(w), _d(f), w.size, C.byref(mean), C.byref(se))
+    return mean.value, se.value
+
+
+def proposal_grid(dims, b2_max, E, v, j, mean, std):
+    dims = _arr(dims, np.int32)
+    n = int(np.prod(dims))
+    x = np.zeros((n, 8))
+    lib().oracle_proposal_grid(_i32(dims), float(b2_max), float(E), int(v), int(j),
+                               _d(_arr(mean, np.float64)), _d(_arr(std, np.float64)), _d(x))
+    return x

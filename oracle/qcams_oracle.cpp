@@ -977,50 +977,55 @@ void oracle_reduce(int64_t n, const int32_t* cls, const int32_t* vt, const int32
 }
 
 // Cross sections from the histograms, Sec. 2.3 (opacity P = N_x / N with the
-// binomial error delta) and Eq. for sigma in Sec. 4 read as
-// sigma_x = 2 pi int P_x(b) b db (the printed prefactor is garbled), evaluated
-// as 2 pi sum_c w_c b_c P_x(c) with caller-given quadrature weights w_c; the
-// standard error is 2 pi sqrt(sum_c (w_c b_c delta_c)^2).  N excludes FAIL.
-// Weighted mode uses P = sum w 1_x / N and its sample standard error.
-// out: per cell [6 classes][P, delta] then per group [6][sigma, SE].
+// binomial error delta, Eq. 16) and the cross-section integral of Sec. 4 read
+// as sigma_x = 2 pi int P_x(b) b db (the printed prefactor is garbled),
+// evaluated as 2 pi sum_c w_c b_c P_x(c) with caller-given quadrature
+// weights w_c; the standard error is 2 pi sqrt(sum_c (w_c b_c delta_c)^2).
+// N excludes FAIL.  Entries k = 0..5 are the classes, k = 6 the reactive
+// total R_AC + R_BC.  Weighted mode uses P = sum w 1_x / N and its sample
+// standard error.  out: per cell [7][P, delta] then per group [7][sigma, SE].
 void oracle_xsec(const int64_t* hist, int32_t n_cells, const double* cell_b,
                  const double* cell_w, const int32_t* group, int32_t n_groups,
                  int32_t weighted, double* out) {
-  double* grp = out + 12 * (size_t)n_cells;
-  std::memset(grp, 0, sizeof(double) * 12 * (size_t)n_groups);
-  double* var = new double[6 * (size_t)(n_groups > 0 ? n_groups : 1)]();
+  const int NE = 7;
+  double* grp = out + 2 * NE * (size_t)n_cells;
+  std::memset(grp, 0, sizeof(double) * 2 * NE * (size_t)n_groups);
+  double* var = new double[NE * (size_t)(n_groups > 0 ? n_groups : 1)]();
   for (int c = 0; c < n_cells; ++c) {
     const int64_t* H = hist + (int64_t)H_STRIDE * c;
     double N = 0.0;
     for (int k = 0; k < 5; ++k) N += double(H[H_COUNT + k]);
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NE; ++k) {
+      // the reactive total: classes R_AC (1) and R_BC (2) are exclusive
+      double Nx = k < 6 ? double(H[H_COUNT + k]) : double(H[H_COUNT + 1] + H[H_COUNT + 2]);
+      double swf = k < 6 ? double(H[H_W + k]) : double(H[H_W + 1] + H[H_W + 2]);
+      double sw2f = k < 6 ? double(H[H_W2 + k]) : double(H[H_W2 + 1] + H[H_W2 + 2]);
       double P = 0.0, d = 0.0;
       if (N > 0) {
         if (!weighted) {
-          double Nx = double(H[H_COUNT + k]);
           P = Nx / N;
           d = std::sqrt(Nx) / N * std::sqrt((N - Nx) / N);
         } else {
-          double sw = std::ldexp(double(H[H_W + k]), -32);
-          double sw2 = std::ldexp(double(H[H_W2 + k]), -32);
+          double sw = std::ldexp(swf, -32);
+          double sw2 = std::ldexp(sw2f, -32);
           P = sw / N;
           double m2 = sw2 / N;
           d = N > 1 ? std::sqrt(std::max(0.0, m2 - P * P) / (N - 1.0)) : 0.0;
         }
       }
-      out[12 * (size_t)c + 2 * k] = P;
-      out[12 * (size_t)c + 2 * k + 1] = d;
+      out[2 * NE * (size_t)c + 2 * k] = P;
+      out[2 * NE * (size_t)c + 2 * k + 1] = d;
       int g = group[c];
       if (g >= 0 && g < n_groups) {
         double wb = cell_w[c] * cell_b[c];
-        grp[12 * (size_t)g + 2 * k] += 2.0 * kPi * wb * P;
-        var[6 * (size_t)g + k] += (wb * d) * (wb * d);
+        grp[2 * NE * (size_t)g + 2 * k] += 2.0 * kPi * wb * P;
+        var[NE * (size_t)g + k] += (wb * d) * (wb * d);
       }
     }
   }
   for (int g = 0; g < n_groups; ++g)
-    for (int k = 0; k < 6; ++k)
-      grp[12 * (size_t)g + 2 * k + 1] = 2.0 * kPi * std::sqrt(var[6 * (size_t)g + k]);
+    for (int k = 0; k < NE; ++k)
+      grp[2 * NE * (size_t)g + 2 * k + 1] = 2.0 * kPi * std::sqrt(var[NE * (size_t)g + k]);
   delete[] var;
 }
 

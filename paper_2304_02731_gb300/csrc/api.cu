@@ -1022,41 +1022,47 @@ int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_
   if (e != cudaSuccess) return QCAMS_E_CUDA;
   // Opacity and binomial error per cell (Eqs. 13, 16); cross sections per
   // group as 2 pi sum w b P (Eq. 18 with the angular measure divided out).
+  // Entry 6 is the reactive total R_AC + R_BC (exclusive classes, so its
+  // counts and weight sums are the sums of the two channels').
   const int nc = cells->n_cells, ng = cells->n_groups;
-  std::vector<double> var(6 * (size_t)(ng > 0 ? ng : 1), 0.0);
-  double* grp = xsec_out + 12 * (size_t)nc;
-  for (size_t k = 0; k < 12 * (size_t)ng; ++k) grp[k] = 0.0;
+  const int NE = QCAMS_XSEC_ENTRIES;
+  std::vector<double> var(NE * (size_t)(ng > 0 ? ng : 1), 0.0);
+  double* grp = xsec_out + 2 * NE * (size_t)nc;
+  for (size_t k = 0; k < 2 * NE * (size_t)ng; ++k) grp[k] = 0.0;
   for (int c = 0; c < nc; ++c) {
     const int64_t* h = H.data() + (size_t)c * QCAMS_H_STRIDE;
     double N = 0.0;
     for (int k = 0; k < 5; ++k) N += (double)h[QCAMS_H_COUNT + k];
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < NE; ++k) {
+      auto sum = [&](int off) {
+        return k < 6 ? (double)h[off + k] : (double)h[off + 1] + (double)h[off + 2];
+      };
       double P = 0.0, dl = 0.0;
       if (N > 0) {
         if (!cells->weighted) {
-          const double Nx = (double)h[QCAMS_H_COUNT + k];
+          const double Nx = sum(QCAMS_H_COUNT);
           P = Nx / N;
           dl = std::sqrt(Nx) / N * std::sqrt((N - Nx) / N);
         } else {
-          const double sw = std::ldexp((double)h[QCAMS_H_W + k], -32);
-          const double sw2 = std::ldexp((double)h[QCAMS_H_W2 + k], -32);
+          const double sw = std::ldexp(sum(QCAMS_H_W), -32);
+          const double sw2 = std::ldexp(sum(QCAMS_H_W2), -32);
           P = sw / N;
           dl = N > 1 ? std::sqrt(std::fmax(0.0, sw2 / N - P * P) / (N - 1.0)) : 0.0;
         }
       }
-      xsec_out[12 * (size_t)c + 2 * k] = P;
-      xsec_out[12 * (size_t)c + 2 * k + 1] = dl;
+      xsec_out[2 * NE * (size_t)c + 2 * k] = P;
+      xsec_out[2 * NE * (size_t)c + 2 * k + 1] = dl;
       const int g = ng > 0 ? cells->group[c] : -1;
       if (g >= 0 && g < ng) {
         const double wb = cells->w[c] * cells->b[c];
-        grp[12 * (size_t)g + 2 * k] += 2.0 * kPi * wb * P;
-        var[6 * (size_t)g + k] += (wb * dl) * (wb * dl);
+        grp[2 * NE * (size_t)g + 2 * k] += 2.0 * kPi * wb * P;
+        var[NE * (size_t)g + k] += (wb * dl) * (wb * dl);
       }
     }
   }
   for (int g = 0; g < ng; ++g)
-    for (int k = 0; k < 6; ++k)
-      grp[12 * (size_t)g + 2 * k + 1] = 2.0 * kPi * std::sqrt(var[6 * (size_t)g + k]);
+    for (int k = 0; k < NE; ++k)
+      grp[2 * NE * (size_t)g + 2 * k + 1] = 2.0 * kPi * std::sqrt(var[NE * (size_t)g + k]);
   return QCAMS_OK;
 }
 

@@ -1,0 +1,810 @@
+// Learned importance-sampling proposal: a small MLP trained on the method's
+// own (initial condition -> outcome) data, turned into a defensive-mixture
+// proposal over (b^2, cos theta, phi, eta, chi) whose likelihood-ratio
+// weights keep the cross-section estimator unbiased (every sampled
+// trajectory is still integrated exactly).
+//
+// Tensor-core design (sm_103a, warp-level mma.sync m16n8k16, BF16 inputs,
+// FP32 accumulation): each warp carries 16 samples through the network.  The
+// accumulator fragment of two adjacent 16x8 output tiles has exactly the
+// register layout of the A operand of a 16x16 slice, so a layer's SiLU output
+// is fed to the next layer's products without touching shared memory.  The
+// backward pass reuses the same fragments: dA = dZ W uses transposed weights
+// staged in shared memory; dW = dZ^T A takes dZ^T and A^T from per-warp
+// shared tiles written during the pass.  Per-CTA FP32 gradient accumulators
+// in shared memory are flushed to global memory once per CTA.
+//
+// The network is ~9k multiply-adds per sample: negligible next to the
+// trajectory integration, so a warp-level mma kernel is enough here.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "qcams.h"
+#include "qcams_device.cuh"
+
+namespace qcams {
+namespace {
+
+constexpr int IN = 8, H = 64, OUT = 4, NP = QCAMS_MLP_NPARAMS;
+constexpr int OW1 = 0, OB1 = OW1 + H * IN, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 + H,
+              OB3 = OW3 + H * H, OW4 = OB3 + H, OB4 = OW4 + OUT * H;
+static_assert(OB4 + OUT == NP, "parameter layout");
+constexpr int WARPS = 4, THREADS = WARPS * 32;
+constexpr double kPi = 3.14159265358979323846;
+
+struct Std {
+  float mean[8], inv_std[8];
+};
+
+// Shared-memory weight tiles (BF16).  Forward B operands use W as [N][K];
+// backward dA = dZ W needs W^T as [K][N].  Padding: W1 K 8 -> 16, W4 N 4 -> 8
+// (forward) and W4^T N 4 -> 16.
+struct WeightsSmem {
+  __nv_bfloat16 w1[H][16];
+  __nv_bfloat16 w2[H][H];
+  __nv_bfloat16 w3[H][H];
+  __nv_bfloat16 w4[8][H];
+  __nv_bfloat16 w2t[H][H];
+  __nv_bfloat16 w3t[H][H];
+  __nv_bfloat16 w4t[H][16];
+  float b1[H], b2[H], b3[H], b4[8];
+};
+struct WarpSmem {
+  float z[3][32][32];          // pre-activations of layers 1-3, fragment order [i][lane]
+  __nv_bfloat16 xt[16][16];    // X^T  [feature (padded)][sample]
+  __nv_bfloat16 at[3][H][16];  // A1^T, A2^T, A3^T [unit][sample]
+  __nv_bfloat16 dzt[H][16];    // dZ^T [unit][sample]
+};
+struct TrainSmem {
+  WeightsSmem w;
+  float grad[NP];
+  WarpSmem warp[WARPS];
+};
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ uint32_t ld2(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// D += A B for one m16n8k16 tile (BF16 in, FP32 accumulate).
+__device__ __forceinline__ void mma(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigm(z); }
+__device__ __forceinline__ float dsilu(float z) {
+  const float s = sigm(z);
+  return s * (1.0f + z * (1.0f - s));
+}
+
+__device__ void load_weights(WeightsSmem& W, const __nv_bfloat16* p, const float* pf) {
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
+    const int r = i / 16, c = i % 16;
+    W.w1[r][c] = c < IN ? p[OW1 + r * IN + c] : zero;
+  }
+  for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
+    const int r = i / H, c = i % H;
+    W.w2[r][c] = p[OW2 + i];
+    W.w3[r][c] = p[OW3 + i];
+    W.w2t[c][r] = p[OW2 + i];
+    W.w3t[c][r] = p[OW3 + i];
+  }
+  for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
+    const int r = i / H, c = i % H;
+    W.w4[r][c] = r < OUT ? p[OW4 + r * H + c] : zero;
+  }
+  for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
+    const int r = i / 16, c = i % 16;
+    W.w4t[r][c] = c < OUT ? p[OW4 + c * H + r] : zero;
+  }
+  for (int i = threadIdx.x; i < H; i += blockDim.x) {
+    W.b1[i] = pf[OB1 + i];
+    W.b2[i] = pf[OB2 + i];
+    W.b3[i] = pf[OB3 + i];
+  }
+  if (threadIdx.x < 8) W.b4[threadIdx.x] = threadIdx.x < OUT ? pf[OB4 + threadIdx.x] : 0.0f;
+}
+
+// Features of the 16 rows handled by this lane's fragment rows: either from
+// x[n][8] or (proposal mode) from the centre of grid cell `row`.
+struct CellGrid {
+  int n_b2, n_cth, n_phi, n_eta, n_chi;
+  float E, v, j, b2_max;
+};
+__device__ __forceinline__ void features(const float* x, int64_t n, int64_t row,
+                                         const CellGrid* grid, float* f) {
+  if (row >= n) {
+    for (int k = 0; k < IN; ++k) f[k] = 0.0f;
+    return;
+  }
+  if (!grid) {
+    for (int k = 0; k < IN; ++k) f[k] = x[row * IN + k];
+    return;
+  }
+  int64_t c = row;
+  const int i_chi = (int)(c % grid->n_chi); c /= grid->n_chi;
+  const int i_eta = (int)(c % grid->n_eta); c /= grid->n_eta;
+  const int i_phi = (int)(c % grid->n_phi); c /= grid->n_phi;
+  const int i_cth = (int)(c % grid->n_cth); c /= grid->n_cth;
+  const int i_b2 = (int)c;
+  f[0] = grid->E;
+  f[1] = sqrtf(grid->b2_max * (i_b2 + 0.5f) / grid->n_b2);
+  f[2] = grid->v;
+  f[3] = grid->j;
+  f[4] = acosf(2.0f * (i_cth + 0.5f) / grid->n_cth - 1.0f);
+  f[5] = 2.0f * (float)kPi * (i_phi + 0.5f) / grid->n_phi;
+  f[6] = (i_chi + 0.5f) / grid->n_chi;
+  f[7] = 2.0f * (float)kPi * (i_eta + 0.5f) / grid->n_eta;
+}
+
+// Forward pass of 16 samples (rows base .. base+15) by one warp.  Returns the
+// logits fragment (rows g and g+8, columns 2q, 2q+1 of the padded 16x8 tile).
+// With TRAIN, pre-activations and transposed activations are kept in the
+// warp's shared tiles for the backward pass.
+template <bool TRAIN>
+__device__ void forward16(const WeightsSmem& W, WarpSmem* ws, const float* x, int64_t n,
+                          int64_t base, const CellGrid* grid, const Std& sd, float* logit) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  float f0[IN], f1[IN];
+  features(x, n, base + g, grid, f0);
+  features(x, n, base + g + 8, grid, f1);
+  for (int k = 0; k < IN; ++k) {
+    f0[k] = (f0[k] - sd.mean[k]) * sd.inv_std[k];
+    f1[k] = (f1[k] - sd.mean[k]) * sd.inv_std[k];
+    if (base + g >= n) f0[k] = 0.0f;
+    if (base + g + 8 >= n) f1[k] = 0.0f;
+  }
+  uint32_t a[4][4];  // A fragments of the current layer input (up to 4 k-slices)
+  a[0][0] = pack2(f0[2 * q], f0[2 * q + 1]);
+  a[0][1] = pack2(f1[2 * q], f1[2 * q + 1]);
+  a[0][2] = 0u;
+  a[0][3] = 0u;
+  if (TRAIN) {
+    ws->xt[2 * q][g] = __float2bfloat16(f0[2 * q]);
+    ws->xt[2 * q + 1][g] = __float2bfloat16(f0[2 * q + 1]);
+    ws->xt[2 * q][g + 8] = __float2bfloat16(f1[2 * q]);
+    ws->xt[2 * q + 1][g + 8] = __float2bfloat16(f1[2 * q + 1]);
+    ws->xt[8 + 2 * q][g] = ws->xt[8 + 2 * q + 1][g] = __float2bfloat16(0.0f);
+    ws->xt[8 + 2 * q][g + 8] = ws->xt[8 + 2 * q + 1][g + 8] = __float2bfloat16(0.0f);
+  }
+  float c[8][4];
+  for (int layer = 0; layer < 3; ++layer) {
+    const float* bias = layer == 0 ? W.b1 : layer == 1 ? W.b2 : W.b3;
+    const int ks = layer == 0 ? 1 : 4;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      c[t][0] = c[t][2] = bias[8 * t + 2 * q];
+      c[t][1] = c[t][3] = bias[8 * t + 2 * q + 1];
+      for (int s = 0; s < ks; ++s) {
+        const __nv_bfloat16* wr = layer == 0 ? &W.w1[8 * t + g][0]
+                                  : layer == 1 ? &W.w2[8 * t + g][16 * s]
+                                               : &W.w3[8 * t + g][16 * s];
+        mma(c[t], a[s], ld2(wr + 2 * q), ld2(wr + 8 + 2 * q));
+      }
+    }
+    if (TRAIN) {
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ws->z[layer][4 * t + e][lane] = c[t][e];
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const float v0 = silu(c[2 * s][0]), v1 = silu(c[2 * s][1]), v2 = silu(c[2 * s][2]),
+                  v3 = silu(c[2 * s][3]);
+      const float w0 = silu(c[2 * s + 1][0]), w1 = silu(c[2 * s + 1][1]),
+                  w2 = silu(c[2 * s + 1][2]), w3 = silu(c[2 * s + 1][3]);
+      a[s][0] = pack2(v0, v1);
+      a[s][1] = pack2(v2, v3);
+      a[s][2] = pack2(w0, w1);
+      a[s][3] = pack2(w2, w3);
+      if (TRAIN) {
+        const int c0 = 16 * s + 2 * q, c1 = 16 * s + 8 + 2 * q;
+        ws->at[layer][c0][g] = __float2bfloat16(v0);
+        ws->at[layer][c0 + 1][g] = __float2bfloat16(v1);
+        ws->at[layer][c0][g + 8] = __float2bfloat16(v2);
+        ws->at[layer][c0 + 1][g + 8] = __float2bfloat16(v3);
+        ws->at[layer][c1][g] = __float2bfloat16(w0);
+        ws->at[layer][c1 + 1][g] = __float2bfloat16(w1);
+        ws->at[layer][c1][g + 8] = __float2bfloat16(w2);
+        ws->at[layer][c1 + 1][g + 8] = __float2bfloat16(w3);
+      }
+    }
+  }
+  logit[0] = logit[2] = W.b4[2 * q];
+  logit[1] = logit[3] = W.b4[2 * q + 1];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const __nv_bfloat16* wr = &W.w4[g][16 * s];
+    mma(logit, a[s], ld2(wr + 2 * q), ld2(wr + 8 + 2 * q));
+  }
+}
+
+// Softmax over the 4 logits of one row held by lanes q = 0 (columns 0, 1)
+// and q = 1 (columns 2, 3); returns this lane's two probabilities.
+__device__ __forceinline__ void softmax_pair(float z0, float z1, float* p0, float* p1) {
+  const float o0 = __shfl_xor_sync(0xffffffffu, z0, 1);
+  const float o1 = __shfl_xor_sync(0xffffffffu, z1, 1);
+  const float m = fmaxf(fmaxf(z0, z1), fmaxf(o0, o1));
+  const float e0 = __expf(z0 - m), e1 = __expf(z1 - m);
+  const float s = e0 + e1 + __expf(o0 - m) + __expf(o1 - m);
+  *p0 = e0 / s;
+  *p1 = e1 / s;
+}
+
+// dW (+)= dZ^T A for one layer: M = n_out (16-row tiles), K = 16 samples,
+// N = n_in (8-column tiles), into the CTA gradient accumulator.
+__device__ void accumulate_dw(const WarpSmem* ws, const __nv_bfloat16 (*aT)[16], int m_tiles,
+                              int n_tiles, int n_out_valid, int n_in, float* gW) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  for (int mt = 0; mt < m_tiles; ++mt) {
+    uint32_t a[4];
+    a[0] = ld2(&ws->dzt[16 * mt + g][2 * q]);
+    a[1] = ld2(&ws->dzt[16 * mt + g + 8][2 * q]);
+    a[2] = ld2(&ws->dzt[16 * mt + g][8 + 2 * q]);
+    a[3] = ld2(&ws->dzt[16 * mt + g + 8][8 + 2 * q]);
+    for (int nt = 0; nt < n_tiles; ++nt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      mma(d, a, ld2(&aT[8 * nt + g][2 * q]), ld2(&aT[8 * nt + g][8 + 2 * q]));
+      const int r0 = 16 * mt + g, r1 = r0 + 8, col = 8 * nt + 2 * q;
+      if (r0 < n_out_valid && col < n_in) {
+        atomicAdd(&gW[r0 * n_in + col], d[0]);
+        atomicAdd(&gW[r0 * n_in + col + 1], d[1]);
+      }
+      if (r1 < n_out_valid && col < n_in) {
+        atomicAdd(&gW[r1 * n_in + col], d[2]);
+        atomicAdd(&gW[r1 * n_in + col + 1], d[3]);
+      }
+    }
+  }
+}
+
+// Write dZ (fragment layout, 16 samples x 8 t-tiles) transposed into dzt.
+__device__ __forceinline__ void store_dzt(WarpSmem* ws, const float (*dz)[4], int tiles) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  for (int t = 0; t < tiles; ++t) {
+    const int c0 = 8 * t + 2 * q;
+    ws->dzt[c0][g] = __float2bfloat16(dz[t][0]);
+    ws->dzt[c0 + 1][g] = __float2bfloat16(dz[t][1]);
+    ws->dzt[c0][g + 8] = __float2bfloat16(dz[t][2]);
+    ws->dzt[c0 + 1][g + 8] = __float2bfloat16(dz[t][3]);
+  }
+}
+
+// Bias gradient: sum over the 16 samples of dZ columns.
+__device__ __forceinline__ void accumulate_db(const float (*dz)[4], int tiles, int n_valid,
+                                              float* gb) {
+  const int lane = threadIdx.x & 31, q = lane & 3;
+  for (int t = 0; t < tiles; ++t) {
+    float s0 = dz[t][0] + dz[t][2], s1 = dz[t][1] + dz[t][3];
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    const int col = 8 * t + 2 * q;
+    if (lane < 4 && col < n_valid) {
+      atomicAdd(&gb[col], s0);
+      if (col + 1 < n_valid) atomicAdd(&gb[col + 1], s1);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, const float* pf,
+                                                      Std sd, const float* x,
+                                                      const uint8_t* label, int64_t n,
+                                                      float* grad, float* loss) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+  load_weights(S.w, pb, pf);
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) S.grad[i] = 0.0f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  WarpSmem* ws = &S.warp[warp];
+  for (int i = lane; i < H * 16; i += 32) (&ws->dzt[0][0])[i] = __float2bfloat16(0.0f);
+  __syncthreads();
+  const float inv_n = 1.0f / (float)n;
+  float loss_acc = 0.0f;
+  const int64_t chunks = (n + 15) / 16;
+  for (int64_t ch = (int64_t)blockIdx.x * WARPS + warp; ch < chunks;
+       ch += (int64_t)gridDim.x * WARPS) {
+    const int64_t base = ch * 16;
+    float lg[4];
+    forward16<true>(S.w, ws, x, n, base, nullptr, sd, lg);
+    // softmax cross-entropy and dZ4 = (p - onehot) / n
+    float dz4[1][4] = {{0.f, 0.f, 0.f, 0.f}};
+    float p[4];
+    softmax_pair(lg[0], lg[1], &p[0], &p[1]);
+    softmax_pair(lg[2], lg[3], &p[2], &p[3]);
+    if (q < 2) {
+      const int64_t r0 = base + g, r1 = base + g + 8;
+      int l0 = r0 < n ? (int)label[r0] : -1, l1 = r1 < n ? (int)label[r1] : -1;
+      if (l0 >= OUT) l0 = -1;   // AMBIG / FAIL lanes carry no target
+      if (l1 >= OUT) l1 = -1;
+      for (int e = 0; e < 2; ++e) {
+        const int col = 2 * q + e;
+        if (l0 >= 0) {
+          dz4[0][e] = (p[e] - (col == l0 ? 1.0f : 0.0f)) * inv_n;
+          if (col == l0) loss_acc -= __logf(fmaxf(p[e], 1e-30f)) * inv_n;
+        }
+        if (l1 >= 0) {
+          dz4[0][2 + e] = (p[2 + e] - (col == l1 ? 1.0f : 0.0f)) * inv_n;
+          if (col == l1) loss_acc -= __logf(fmaxf(p[2 + e], 1e-30f)) * inv_n;
+        }
+      }
+    }
+    // output layer gradients
+    __syncwarp();
+    store_dzt(ws, dz4, 1);
+    __syncwarp();
+    accumulate_dw(ws, ws->at[2], 1, 8, OUT, H, &S.grad[OW4]);
+    accumulate_db(dz4, 1, OUT, &S.grad[OB4]);
+    // dA3 = dZ4 W4: A operand from the dZ4 fragment (K padded 8 -> 16)
+    uint32_t a[4][4];
+    a[0][0] = pack2(dz4[0][0], dz4[0][1]);
+    a[0][1] = pack2(dz4[0][2], dz4[0][3]);
+    a[0][2] = 0u;
+    a[0][3] = 0u;
+    float dz[8][4];
+    for (int layer = 2; layer >= 0; --layer) {
+      const int ks = layer == 2 ? 1 : 4;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        dz[t][0] = dz[t][1] = dz[t][2] = dz[t][3] = 0.0f;
+        for (int s = 0; s < ks; ++s) {
+          const __nv_bfloat16* wr = layer == 2 ? &S.w.w4t[8 * t + g][0]
+                                    : layer == 1 ? &S.w.w3t[8 * t + g][16 * s]
+                                                 : &S.w.w2t[8 * t + g][16 * s];
+          mma(dz[t], a[s], ld2(wr + 2 * q), ld2(wr + 8 + 2 * q));
+        }
+        // dZ = dA * SiLU'(Z)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) dz[t][e] *= dsilu(ws->z[layer][4 * t + e][lane]);
+      }
+      __syncwarp();
+      store_dzt(ws, dz, 8);
+      __syncwarp();
+      float* gW = layer == 2 ? &S.grad[OW3] : layer == 1 ? &S.grad[OW2] : &S.grad[OW1];
+      float* gb = layer == 2 ? &S.grad[OB3] : layer == 1 ? &S.grad[OB2] : &S.grad[OB1];
+      if (layer > 0) accumulate_dw(ws, ws->at[layer - 1], 4, 8, H, H, gW);
+      else accumulate_dw(ws, ws->xt, 4, 1, H, IN, gW);
+      accumulate_db(dz, 8, H, gb);
+      if (layer > 0) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          a[s][0] = pack2(dz[2 * s][0], dz[2 * s][1]);
+          a[s][1] = pack2(dz[2 * s][2], dz[2 * s][3]);
+          a[s][2] = pack2(dz[2 * s + 1][0], dz[2 * s + 1][1]);
+          a[s][3] = pack2(dz[2 * s + 1][2], dz[2 * s + 1][3]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
+  if (lane == 0 && loss) atomicAdd(loss, loss_acc);
+  __syncthreads();
+  for (int i = threadIdx.x; i < NP; i += blockDim.x)
+    if (S.grad[i] != 0.0f) atomicAdd(&grad[i], S.grad[i]);
+}
+
+__global__ void __launch_bounds__(THREADS) k_mlp_infer(const __nv_bfloat16* pb, const float* pf,
+                                                       Std sd, const float* x, int64_t n,
+                                                       CellGrid grid, int use_grid,
+                                                       float* probs, double* g_out,
+                                                       double eps) {
+  __shared__ WeightsSmem W;
+  load_weights(W, pb, pf);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int64_t chunks = (n + 15) / 16;
+  for (int64_t ch = (int64_t)blockIdx.x * WARPS + warp; ch < chunks;
+       ch += (int64_t)gridDim.x * WARPS) {
+    const int64_t base = ch * 16;
+    float lg[4], p[4];
+    forward16<false>(W, nullptr, x, n, base, use_grid ? &grid : nullptr, sd, lg);
+    softmax_pair(lg[0], lg[1], &p[0], &p[1]);
+    softmax_pair(lg[2], lg[3], &p[2], &p[3]);
+    const int64_t r0 = base + g, r1 = base + g + 8;
+    if (probs && q < 2) {
+      if (r0 < n) { probs[r0 * 4 + 2 * q] = p[0]; probs[r0 * 4 + 2 * q + 1] = p[1]; }
+      if (r1 < n) { probs[r1 * 4 + 2 * q] = p[2]; probs[r1 * 4 + 2 * q + 1] = p[3]; }
+    }
+    if (g_out) {
+      // p_R = P(R_AC) + P(R_BC): columns 1 (lane q = 0) and 2 (lane q = 1)
+      const float mine0 = q == 0 ? p[1] : p[0], mine1 = q == 0 ? p[3] : p[2];
+      const float other0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+      const float other1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+      if (q == 0) {
+        if (r0 < n) g_out[r0] = sqrt(eps + (double)mine0 + (double)other0);
+        if (r1 < n) g_out[r1] = sqrt(eps + (double)mine1 + (double)other1);
+      }
+    }
+  }
+}
+
+__global__ void k_adam(float* p, float* m, float* v, const float* grad, __nv_bfloat16* pb,
+                       float lr, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NP; i += gridDim.x * blockDim.x) {
+    const float gr = grad[i];
+    const float mi = 0.9f * m[i] + 0.1f * gr;
+    const float vi = 0.999f * v[i] + 0.001f * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + 1e-8f);
+    p[i] = pi;
+    pb[i] = __float2bfloat16(pi);
+  }
+}
+
+__global__ void k_mlp_init(float* p, float* m, float* v, __nv_bfloat16* pb, uint64_t seed) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NP; i += gridDim.x * blockDim.x) {
+    float fan_in = 0.0f;
+    if (i < OB1) fan_in = IN;
+    else if (i >= OW2 && i < OB2) fan_in = H;
+    else if (i >= OW3 && i < OB3) fan_in = H;
+    else if (i >= OW4 && i < OB4) fan_in = H;
+    float val = 0.0f;
+    if (fan_in > 0.0f) {
+      const uint4 w = philox4x32_10(make_uint4((uint32_t)i, 0u, 3u, 0u),
+                                    make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+      const float u = (float)u01(w.x);
+      val = (2.0f * u - 1.0f) * rsqrtf(fan_in);
+    }
+    p[i] = val;
+    m[i] = 0.0f;
+    v[i] = 0.0f;
+    pb[i] = __float2bfloat16(val);
+  }
+}
+
+__global__ void k_mlp_sync(const float* p, __nv_bfloat16* pb) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NP; i += gridDim.x * blockDim.x)
+    pb[i] = __float2bfloat16(p[i]);
+}
+
+__global__ void k_features(int64_t n, const double* E, const double* b, const int32_t* v,
+                           const int32_t* j, const double* u0, const double* u1,
+                           const double* u2, const double* u3, float* x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i * 8 + 0] = (float)E[i];
+  x[i * 8 + 1] = (float)b[i];
+  x[i * 8 + 2] = (float)v[i];
+  x[i * 8 + 3] = (float)j[i];
+  x[i * 8 + 4] = (float)acos(fmin(1.0, fmax(-1.0, 2.0 * u0[i] - 1.0)));
+  x[i * 8 + 5] = (float)(2.0 * kPi * u1[i]);
+  x[i * 8 + 6] = (float)u3[i];
+  x[i * 8 + 7] = (float)(2.0 * kPi * u2[i]);
+}
+
+__global__ void k_moments(const float* x, int64_t n, double* acc) {
+  __shared__ double s[16];
+  if (threadIdx.x < 16) s[threadIdx.x] = 0.0;
+  __syncthreads();
+  double loc[16] = {0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < 8; ++k) {
+      const double v = x[i * 8 + k];
+      loc[k] += v;
+      loc[8 + k] += v * v;
+    }
+  for (int k = 0; k < 16; ++k) atomicAdd(&s[k], loc[k]);
+  __syncthreads();
+  if (threadIdx.x < 16) atomicAdd(&acc[threadIdx.x], s[threadIdx.x]);
+}
+
+// Normalise the proposal and form its integer CDF in one block with a fixed
+// summation order (deterministic bits).  g holds g_c on entry, q_c on exit.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_proposal_finish(double* g, int64_t n_cells,
+                                                                  double alpha, int64_t* qfix,
+                                                                  int64_t* cdf) {
+  __shared__ double ds[kScanThreads];
+  __shared__ long long ls[kScanThreads];
+  const int t = threadIdx.x;
+  const int64_t per = (n_cells + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = t * per, hi = min(n_cells, lo + per);
+  double sum = 0.0;
+  for (int64_t c = lo; c < hi; ++c) sum += g[c];
+  ds[t] = sum;
+  __syncthreads();
+  for (int o = kScanThreads / 2; o > 0; o >>= 1) {
+    if (t < o) ds[t] += ds[t + o];
+    __syncthreads();
+  }
+  const double total = ds[0];
+  long long part = 0;
+  for (int64_t c = lo; c < hi; ++c) {
+    const double qc = alpha / (double)n_cells + (1.0 - alpha) * g[c] / total;
+    g[c] = qc;
+    const long long qi = __double2ll_rn(qc * 1099511627776.0);  // 2^40
+    qfix[c] = qi;
+    part += qi;
+  }
+  ls[t] = part;
+  __syncthreads();
+  // inclusive scan of the per-thread parts (Hillis-Steele)
+  for (int o = 1; o < kScanThreads; o <<= 1) {
+    long long v = t >= o ? ls[t - o] : 0;
+    __syncthreads();
+    ls[t] += v;
+    __syncthreads();
+  }
+  long long run = t > 0 ? ls[t - 1] : 0;
+  for (int64_t c = lo; c < hi; ++c) {
+    run += qfix[c];
+    cdf[c] = run;
+  }
+}
+
+__global__ void k_sample(CellGrid grid, int64_t n_cells, const int64_t* qfix, const int64_t* cdf,
+                         int64_t n, uint64_t seed, uint64_t id_offset, double b2_max, double* b,
+                         double* u0, double* u1, double* u2, double* u3, double* w,
+                         int32_t* cell) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t id = id_offset + (uint64_t)i;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  const uint4 wa = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), 1u, 0u), key);
+  const uint4 wb = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), 2u, 0u), key);
+  const unsigned long long total = (unsigned long long)cdf[n_cells - 1];
+  // U = floor(u_0 total) with u_0 = (w + 1/2) 2^-32, in exact integer arithmetic:
+  // (2 w + 1) total / 2^33
+  const unsigned long long m = 2ull * wa.x + 1ull;
+  const unsigned long long lo = m * total, hi = __umul64hi(m, total);
+  const unsigned long long U = (hi << 31) | (lo >> 33);
+  int64_t a = 0, z = n_cells - 1;
+  while (a < z) {
+    const int64_t mid = (a + z) >> 1;
+    if ((unsigned long long)cdf[mid] > U) z = mid;
+    else a = mid + 1;
+  }
+  int64_t c = a;
+  cell[i] = (int32_t)c;
+  const int i_chi = (int)(c % grid.n_chi); c /= grid.n_chi;
+  const int i_eta = (int)(c % grid.n_eta); c /= grid.n_eta;
+  const int i_phi = (int)(c % grid.n_phi); c /= grid.n_phi;
+  const int i_cth = (int)(c % grid.n_cth); c /= grid.n_cth;
+  const int i_b2 = (int)c;
+  const double b2 = b2_max * (i_b2 + u01(wa.y)) / grid.n_b2;
+  b[i] = sqrt(b2);
+  u0[i] = (i_cth + u01(wa.z)) / grid.n_cth;
+  u1[i] = (i_phi + u01(wa.w)) / grid.n_phi;
+  u2[i] = (i_eta + u01(wb.x)) / grid.n_eta;
+  u3[i] = (i_chi + u01(wb.y)) / grid.n_chi;
+  w[i] = ((double)total / (double)n_cells) / (double)qfix[a];
+}
+
+int dev_ok() {
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QCAMS_E_NODEVICE;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+    return QCAMS_E_NODEVICE;
+  return (major == 10 && minor == 3) ? QCAMS_OK : QCAMS_E_NODEVICE;
+}
+
+bool mlp_ok(const qcams_mlp* m) {
+  return m && m->params && m->adam_m && m->adam_v && m->grad && m->params_bf16;
+}
+
+Std std_of(const qcams_mlp* m) {
+  Std s;
+  for (int k = 0; k < 8; ++k) {
+    s.mean[k] = m->x_mean[k];
+    s.inv_std[k] = m->x_std[k] > 0.f ? 1.0f / m->x_std[k] : 1.0f;
+  }
+  return s;
+}
+
+int sm_count() {
+  int dev = 0, s = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
+  return s > 0 ? s : 1;
+}
+
+int status_of(cudaError_t e) { return e == cudaSuccess ? QCAMS_OK : QCAMS_E_CUDA; }
+
+bool grid_ok(const qcams_proposal_spec* s) {
+  if (!s || s->n_b2 < 1 || s->n_cth < 1 || s->n_phi < 1 || s->n_eta < 1 || s->n_chi < 1)
+    return false;
+  const double n = (double)s->n_b2 * s->n_cth * s->n_phi * s->n_eta * s->n_chi;
+  return n <= (double)(1 << 22) && s->b2_max > 0 && s->alpha > 0 && s->alpha <= 1 &&
+         s->eps >= 0 && std::isfinite(s->E_col);
+}
+
+CellGrid grid_of(const qcams_proposal_spec* s) {
+  CellGrid g;
+  g.n_b2 = s->n_b2;
+  g.n_cth = s->n_cth;
+  g.n_phi = s->n_phi;
+  g.n_eta = s->n_eta;
+  g.n_chi = s->n_chi;
+  g.E = (float)s->E_col;
+  g.v = (float)s->v;
+  g.j = (float)s->j;
+  g.b2_max = (float)s->b2_max;
+  return g;
+}
+
+}  // namespace
+}  // namespace qcams
+
+using namespace qcams;
+
+extern "C" {
+
+int qcams_mlp_init(qcams_mlp* m, uint64_t seed, void* cuda_stream) {
+  if (!mlp_ok(m)) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  for (int k = 0; k < 8; ++k) {
+    m->x_mean[k] = 0.0f;
+    m->x_std[k] = 1.0f;
+  }
+  m->step = 0;
+  (void)cudaGetLastError();
+  k_mlp_init<<<36, 256, 0, (cudaStream_t)cuda_stream>>>(
+      m->params, m->adam_m, m->adam_v, reinterpret_cast<__nv_bfloat16*>(m->params_bf16), seed);
+  return status_of(cudaGetLastError());
+}
+
+int qcams_mlp_sync(const qcams_mlp* m, void* cuda_stream) {
+  if (!mlp_ok(m)) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  (void)cudaGetLastError();
+  k_mlp_sync<<<36, 256, 0, (cudaStream_t)cuda_stream>>>(
+      m->params, reinterpret_cast<__nv_bfloat16*>(m->params_bf16));
+  return status_of(cudaGetLastError());
+}
+
+int qcams_mlp_features(const qcams_batch* batch, const double* E_col, const double* b,
+                       const int32_t* v, const int32_t* j, float* x, void* cuda_stream) {
+  if (!batch || batch->n < 0) return QCAMS_E_INVALID;
+  if (batch->n == 0) return QCAMS_OK;
+  if (!E_col || !b || !v || !j || !x || !batch->u[0] || !batch->u[1] || !batch->u[2] ||
+      !batch->u[3])
+    return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  (void)cudaGetLastError();
+  k_features<<<(unsigned)((batch->n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(
+      batch->n, E_col, b, v, j, batch->u[0], batch->u[1], batch->u[2], batch->u[3], x);
+  return status_of(cudaGetLastError());
+}
+
+int qcams_mlp_fit_standardizer(qcams_mlp* m, const float* x, int64_t n, void* cuda_stream) {
+  if (!m || !x || n < 2) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* acc = nullptr;
+  (void)cudaGetLastError();
+  if (cudaMallocAsync((void**)&acc, 16 * sizeof(double), st) != cudaSuccess) return QCAMS_E_CUDA;
+  cudaError_t e = cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
+  if (e == cudaSuccess) {
+    k_moments<<<sm_count() * 2, 256, 0, st>>>(x, n, acc);
+    e = cudaGetLastError();
+  }
+  double h[16];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(acc, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  for (int k = 0; k < 8; ++k) {
+    const double mu = h[k] / (double)n;
+    const double var = h[8 + k] / (double)n - mu * mu;
+    m->x_mean[k] = (float)mu;
+    m->x_std[k] = var > 1e-20 ? (float)std::sqrt(var) : 1.0f;
+  }
+  return QCAMS_OK;
+}
+
+int qcams_mlp_grad(const qcams_mlp* m, const float* x, const uint8_t* label, int64_t n,
+                   float* loss_out, void* cuda_stream) {
+  if (!mlp_ok(m) || !x || !label || n < 1) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  (void)cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(m->grad, 0, NP * sizeof(float), st);
+  if (e == cudaSuccess && loss_out) e = cudaMemsetAsync(loss_out, 0, sizeof(float), st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  const size_t smem = sizeof(TrainSmem);
+  e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  const int64_t chunks = (n + 15) / 16;
+  int64_t grid = (chunks + WARPS * 8 - 1) / (WARPS * 8);   // ~8 chunks per warp
+  if (grid > sm_count()) grid = sm_count();
+  if (grid < 1) grid = 1;
+  k_mlp_grad<<<(unsigned)grid, THREADS, smem, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(m->params_bf16), m->params, std_of(m), x, label, n,
+      m->grad, loss_out);
+  return status_of(cudaGetLastError());
+}
+
+int qcams_mlp_train_step(qcams_mlp* m, const float* x, const uint8_t* label, int64_t n,
+                         float lr, float* loss_out, void* cuda_stream) {
+  if (!(lr > 0.0f)) return QCAMS_E_INVALID;
+  int rc = qcams_mlp_grad(m, x, label, n, loss_out, cuda_stream);
+  if (rc != QCAMS_OK) return rc;
+  m->step += 1;
+  const float c1 = (float)(1.0 - std::pow(0.9, (double)m->step));
+  const float c2 = (float)(1.0 - std::pow(0.999, (double)m->step));
+  k_adam<<<36, 256, 0, (cudaStream_t)cuda_stream>>>(
+      m->params, m->adam_m, m->adam_v, m->grad,
+      reinterpret_cast<__nv_bfloat16*>(m->params_bf16), lr, c1, c2);
+  return status_of(cudaGetLastError());
+}
+
+int qcams_mlp_infer(const qcams_mlp* m, const float* x, int64_t n, float* probs,
+                    void* cuda_stream) {
+  if (!mlp_ok(m) || !x || !probs || n < 0) return QCAMS_E_INVALID;
+  if (n == 0) return QCAMS_OK;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  (void)cudaGetLastError();
+  const int64_t chunks = (n + 15) / 16;
+  int64_t grid = (chunks + WARPS - 1) / WARPS;
+  if (grid > 8 * sm_count()) grid = 8 * sm_count();
+  CellGrid none{};
+  k_mlp_infer<<<(unsigned)grid, THREADS, 0, (cudaStream_t)cuda_stream>>>(
+      reinterpret_cast<const __nv_bfloat16*>(m->params_bf16), m->params, std_of(m), x, n, none,
+      0, probs, nullptr, 0.0);
+  return status_of(cudaGetLastError());
+}
+
+int qcams_build_proposal(const qcams_mlp* m, const qcams_proposal_spec* spec, double* q,
+                         int64_t* qfix, int64_t* cdf, void* cuda_stream) {
+  if (!mlp_ok(m) || !grid_ok(spec) || !q || !qfix || !cdf) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int64_t N = (int64_t)spec->n_b2 * spec->n_cth * spec->n_phi * spec->n_eta * spec->n_chi;
+  const int64_t chunks = (N + 15) / 16;
+  int64_t grid = (chunks + WARPS - 1) / WARPS;
+  if (grid > 8 * sm_count()) grid = 8 * sm_count();
+  (void)cudaGetLastError();
+  k_mlp_infer<<<(unsigned)grid, THREADS, 0, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(m->params_bf16), m->params, std_of(m), nullptr, N,
+      grid_of(spec), 1, nullptr, q, spec->eps);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  k_proposal_finish<<<1, kScanThreads, 0, st>>>(q, N, spec->alpha, qfix, cdf);
+  return status_of(cudaGetLastError());
+}
+
+int qcams_sample_proposal(const qcams_proposal_spec* spec, const int64_t* qfix,
+                          const int64_t* cdf, int64_t n, uint64_t seed, uint64_t id_offset,
+                          double* b, double* const* u_out, double* w, int32_t* cell,
+                          void* cuda_stream) {
+  if (!grid_ok(spec) || !qfix || !cdf || n < 0 || !b || !u_out || !w || !cell) return QCAMS_E_INVALID;
+  if (!u_out[0] || !u_out[1] || !u_out[2] || !u_out[3]) return QCAMS_E_INVALID;
+  if (n == 0) return QCAMS_OK;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  const int64_t N = (int64_t)spec->n_b2 * spec->n_cth * spec->n_phi * spec->n_eta * spec->n_chi;
+  (void)cudaGetLastError();
+  k_sample<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>(
+      grid_of(spec), N, qfix, cdf, n, seed, id_offset, spec->b2_max, b, u_out[0], u_out[1],
+      u_out[2], u_out[3], w, cell);
+  return status_of(cudaGetLastError());
+}
+
+}  // extern "C"

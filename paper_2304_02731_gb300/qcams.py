@@ -36,7 +36,11 @@ GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
 EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
            "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
-           "qcams_debug_exp", "qcams_autotune"]
+           "qcams_debug_exp", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
+           "qcams_mlp_features", "qcams_mlp_fit_standardizer", "qcams_mlp_grad",
+           "qcams_mlp_train_step", "qcams_mlp_infer", "qcams_build_proposal",
+           "qcams_sample_proposal"]
+MLP_NPARAMS = 9156
 
 
 class QcamsError(RuntimeError):
@@ -88,6 +92,19 @@ class TuneResult(C.Structure):
                 ("lane_steps_per_s", C.c_double)]
 
 
+class CMLP(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("adam_m", C.c_void_p), ("adam_v", C.c_void_p),
+                ("grad", C.c_void_p), ("params_bf16", C.c_void_p), ("x_mean", C.c_float * 8),
+                ("x_std", C.c_float * 8), ("step", C.c_int64)]
+
+
+class ProposalSpec(C.Structure):
+    _fields_ = [("E_col", C.c_double), ("v", C.c_int32), ("j", C.c_int32),
+                ("n_b2", C.c_int32), ("n_cth", C.c_int32), ("n_phi", C.c_int32),
+                ("n_eta", C.c_int32), ("n_chi", C.c_int32), ("pad", C.c_int32),
+                ("b2_max", C.c_double), ("eps", C.c_double), ("alpha", C.c_double)]
+
+
 class Cells(C.Structure):
     _fields_ = [("n_cells", C.c_int32), ("n_groups", C.c_int32), ("b", C.c_void_p),
                 ("w", C.c_void_p), ("group", C.c_void_p), ("weighted", C.c_int32),
@@ -127,6 +144,16 @@ def lib():
                 "qcams_debug_exp": (C.c_int, [V, V, V, I64, V]),
                 "qcams_autotune": (C.c_int, [P(System), I32, P(Integ), P(CBatch), I64,
                                              P(TuneResult), P(I32), P(Integ), V]),
+                "qcams_mlp_init": (C.c_int, [P(CMLP), C.c_uint64, V]),
+                "qcams_mlp_sync": (C.c_int, [P(CMLP), V]),
+                "qcams_mlp_features": (C.c_int, [P(CBatch), V, V, V, V, V, V]),
+                "qcams_mlp_fit_standardizer": (C.c_int, [P(CMLP), V, I64, V]),
+                "qcams_mlp_grad": (C.c_int, [P(CMLP), V, V, I64, V, V]),
+                "qcams_mlp_train_step": (C.c_int, [P(CMLP), V, V, I64, C.c_float, V, V]),
+                "qcams_mlp_infer": (C.c_int, [P(CMLP), V, I64, V, V]),
+                "qcams_build_proposal": (C.c_int, [P(CMLP), P(ProposalSpec), V, V, V, V]),
+                "qcams_sample_proposal": (C.c_int, [P(ProposalSpec), V, V, I64, C.c_uint64,
+                                                    C.c_uint64, V, V, V, V, V]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -344,7 +371,8 @@ def reduce_xsec(batch: Batch, n_cells: int, cell_b=None, cell_w=None, group=None
                 weighted=False, hist_out: torch.Tensor | None = None, stream=None,
                 finalize=True):
     """qcams_reduce_xsec.  Returns (hist [n_cells, H_STRIDE] device tensor,
-    cells [n_cells, 6, 2] and groups [n_groups, 6, 2] host arrays or None)."""
+    cells [n_cells, 7, 2] and groups [n_groups, 7, 2] host arrays or None: entries
+    0..5 the classes, 6 the reactive total R_AC + R_BC)."""
     if hist_out is None:
         hist_out = torch.empty(n_cells * H_STRIDE, dtype=torch.int64, device=batch.device)
     cells = Cells()
@@ -360,7 +388,7 @@ def reduce_xsec(batch: Batch, n_cells: int, cell_b=None, cell_w=None, group=None
         cells.w = cw.ctypes.data
         cells.group = cg.ctypes.data
     cells.weighted = int(bool(weighted))
-    out = np.zeros(12 * n_cells + 12 * n_groups) if finalize else None
+    out = np.zeros(14 * n_cells + 14 * n_groups) if finalize else None
     rc = lib().qcams_reduce_xsec(C.byref(batch.c), C.byref(cells), C.c_void_p(hist_out.data_ptr()),
                                  C.c_void_p(out.ctypes.data) if finalize else None,
                                  _stream(stream))
@@ -368,8 +396,8 @@ def reduce_xsec(batch: Batch, n_cells: int, cell_b=None, cell_w=None, group=None
     hist = hist_out.view(n_cells, H_STRIDE)
     if not finalize:
         return hist, None, None
-    return (hist, out[:12 * n_cells].reshape(n_cells, 6, 2),
-            out[12 * n_cells:].reshape(n_groups, 6, 2))
+    return (hist, out[:14 * n_cells].reshape(n_cells, 7, 2),
+            out[14 * n_cells:].reshape(n_groups, 7, 2))
 
 
 def last_run_stats(stream=None) -> dict:
@@ -433,3 +461,119 @@ def run_workload(wl, integ: Integ | None = None, device="cuda", stream=None, fin
     hist, cells, groups = reduce_xsec(batch, wl.n_cells, wl.cell_b, wl.cell_w, wl.cell_group,
                                       wl.n_groups, stream=stream, finalize=finalize)
     return batch, hist, cells, groups
+
+
+# ---------------------------------------------------------------------------
+# learned importance-sampling proposal
+# ---------------------------------------------------------------------------
+class MLP:
+    """Device storage of the outcome MLP (qcams_mlp) and its entry points."""
+
+    def __init__(self, device="cuda", seed: int = 0):
+        dev = torch.device(device)
+        f = lambda: torch.zeros(MLP_NPARAMS, dtype=torch.float32, device=dev)
+        self.device = dev
+        self.params, self.m, self.v, self.grad = f(), f(), f(), f()
+        self.params_bf16 = torch.zeros(MLP_NPARAMS, dtype=torch.int16, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.c = CMLP()
+        self.c.params = self.params.data_ptr()
+        self.c.adam_m = self.m.data_ptr()
+        self.c.adam_v = self.v.data_ptr()
+        self.c.grad = self.grad.data_ptr()
+        self.c.params_bf16 = self.params_bf16.data_ptr()
+        _check(lib().qcams_mlp_init(C.byref(self.c), int(seed), _stream()), "qcams_mlp_init")
+
+    def set_params(self, values):
+        self.params.copy_(torch.as_tensor(values, dtype=torch.float32))
+        _check(lib().qcams_mlp_sync(C.byref(self.c), _stream()), "qcams_mlp_sync")
+
+    def set_standardizer(self, mean, std):
+        for k in range(8):
+            self.c.x_mean[k] = float(mean[k])
+            self.c.x_std[k] = float(std[k])
+
+    @property
+    def standardizer(self):
+        return np.array(list(self.c.x_mean)), np.array(list(self.c.x_std))
+
+    @property
+    def step(self) -> int:
+        return self.c.step
+
+    def features(self, batch: Batch, E, b, v, j) -> torch.Tensor:
+        return mlp_features(batch, E, b, v, j)
+
+    def fit_standardizer(self, x: torch.Tensor):
+        x = x.contiguous()
+        _check(lib().qcams_mlp_fit_standardizer(C.byref(self.c), x.data_ptr(), x.shape[0],
+                                                _stream()), "qcams_mlp_fit_standardizer")
+
+    def compute_grad(self, x: torch.Tensor, cls: torch.Tensor) -> float:
+        x, cls = x.contiguous(), cls.to(torch.uint8).contiguous()
+        _check(lib().qcams_mlp_grad(C.byref(self.c), x.data_ptr(), cls.data_ptr(), x.shape[0],
+                                    self.loss.data_ptr(), _stream()), "qcams_mlp_grad")
+        return self.loss
+
+    def train_step(self, x: torch.Tensor, cls: torch.Tensor, lr: float):
+        _check(lib().qcams_mlp_train_step(C.byref(self.c), x.data_ptr(), cls.data_ptr(),
+                                          x.shape[0], float(lr), self.loss.data_ptr(),
+                                          _stream()), "qcams_mlp_train_step")
+        return self.loss
+
+    def infer(self, x: torch.Tensor) -> torch.Tensor:
+        x = x.contiguous()
+        probs = torch.empty(x.shape[0], 4, dtype=torch.float32, device=x.device)
+        _check(lib().qcams_mlp_infer(C.byref(self.c), x.data_ptr(), x.shape[0],
+                                     probs.data_ptr(), _stream()), "qcams_mlp_infer")
+        return probs
+
+    def build_proposal(self, spec: ProposalSpec):
+        N = spec.n_b2 * spec.n_cth * spec.n_phi * spec.n_eta * spec.n_chi
+        q = torch.empty(N, dtype=torch.float64, device=self.device)
+        qfix = torch.empty(N, dtype=torch.int64, device=self.device)
+        cdf = torch.empty(N, dtype=torch.int64, device=self.device)
+        _check(lib().qcams_build_proposal(C.byref(self.c), C.byref(spec), q.data_ptr(),
+                                          qfix.data_ptr(), cdf.data_ptr(), _stream()),
+               "qcams_build_proposal")
+        return q, qfix, cdf
+
+
+def proposal_spec(E_col, v, j, dims=(16, 8, 8, 8, 4), b2_max=100.0, eps=1e-3,
+                  alpha=0.2) -> ProposalSpec:
+    s = ProposalSpec()
+    s.E_col, s.v, s.j = float(E_col), int(v), int(j)
+    s.n_b2, s.n_cth, s.n_phi, s.n_eta, s.n_chi = (int(d) for d in dims)
+    s.b2_max, s.eps, s.alpha = float(b2_max), float(eps), float(alpha)
+    return s
+
+
+def sample_proposal(spec: ProposalSpec, qfix: torch.Tensor, cdf: torch.Tensor, n: int,
+                    seed: int, id_offset: int = 0):
+    """qcams_sample_proposal: (b, u[4, n], w, cell) device tensors."""
+    dev = qfix.device
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    u = torch.empty(4, n, dtype=torch.float64, device=dev)
+    w = torch.empty(n, dtype=torch.float64, device=dev)
+    cell = torch.empty(n, dtype=torch.int32, device=dev)
+    uptr = (C.c_void_p * 4)(*[u[k].data_ptr() for k in range(4)])
+    _check(lib().qcams_sample_proposal(C.byref(spec), qfix.data_ptr(), cdf.data_ptr(), int(n),
+                                       int(seed), int(id_offset), b.data_ptr(), uptr,
+                                       w.data_ptr(), cell.data_ptr(), _stream()),
+           "qcams_sample_proposal")
+    return b, u, w, cell
+
+
+def mlp_features(batch: Batch, E, b, v, j) -> torch.Tensor:
+    """qcams_mlp_features: network inputs [n, 8] of initialised lanes."""
+    dev = batch.device
+    tE, _ = _dptr(E, torch.float64, dev)
+    tb, _ = _dptr(b, torch.float64, dev)
+    tv, _ = _dptr(v, torch.int32, dev)
+    tj, _ = _dptr(j, torch.int32, dev)
+    x = torch.empty(batch.n, 8, dtype=torch.float32, device=dev)
+    _check(lib().qcams_mlp_features(C.byref(batch.c), tE.data_ptr(), tb.data_ptr(),
+                                    tv.data_ptr(), tj.data_ptr(), x.data_ptr(), _stream()),
+           "qcams_mlp_features")
+    torch.cuda.current_stream().synchronize()
+    return x

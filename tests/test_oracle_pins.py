@@ -583,12 +583,14 @@ def test_xsec_binomial_error_and_linear_opacity(oracle):
     N = 1000
     for c in range(nc):
         H[c, 0] = 250
-        H[c, 1] = 700
+        H[c, 1] = 670
+        H[c, 2] = 30
         H[c, 3] = 50
         H[c, 5] = 17     # failures are excluded from N
         H[c, 6] = N + 17
     cells, groups = oracle.xsec(H, b, w, np.zeros(nc, np.int32), 1)
-    for k, cnt in [(0, 250), (1, 700), (3, 50)]:
+    # entry 6 is the reactive total R_AC + R_BC
+    for k, cnt in [(0, 250), (1, 670), (2, 30), (3, 50), (6, 700)]:
         p = cnt / N
         assert cells[0, k, 0] == pytest.approx(p, rel=1e-15)
         assert cells[0, k, 1] == pytest.approx(math.sqrt(p * (1 - p) / N), rel=1e-13)
@@ -596,3 +598,24 @@ def test_xsec_binomial_error_and_linear_opacity(oracle):
         se = 2 * math.pi * math.sqrt(sum((wi * bi) ** 2 for wi, bi in zip(w, b))) * \
             math.sqrt(p * (1 - p) / N)
         assert groups[0, k, 1] == pytest.approx(se, rel=1e-13)
+
+
+def test_weighted_xsec_is_the_sample_mean_of_weighted_indicators(oracle):
+    """Importance-weighted mode: P_x = mean(w 1_x) over the non-failed lanes
+    and delta_x its standard error (sample variance / N), per class and for
+    the reactive total; checked against the per-lane definition."""
+    rng = np.random.default_rng(8)
+    n = 4000
+    cls = rng.choice(6, n, p=[0.6, 0.1, 0.08, 0.12, 0.05, 0.05])
+    w = rng.uniform(0.2, 5.0, n)
+    z = np.zeros(n, np.int32)
+    H = oracle.reduce(cls, z, z, np.zeros(n), z, 1, w)
+    cells, groups = oracle.xsec(H, [1.0], [50.0], [0], 1, weighted=True)
+    ok = cls != 5
+    N = ok.sum()
+    for k, sel in [(0, cls == 0), (1, cls == 1), (2, cls == 2), (3, cls == 3),
+                   (6, (cls == 1) | (cls == 2))]:
+        y = (w * sel)[ok]
+        assert cells[0, k, 0] == pytest.approx(y.mean(), rel=1e-9)
+        assert cells[0, k, 1] == pytest.approx(y.std(ddof=1) / math.sqrt(N), rel=1e-9)
+        assert groups[0, k, 0] == pytest.approx(math.pi * 100.0 * y.mean(), rel=1e-9)
