@@ -23,7 +23,11 @@
  *     CUDA device (or managed) memory of the current device; "host" arrays
  *     are ordinary host memory.  The library keeps only a small per-device
  *     context (level table, potential shape table, work counters), created
- *     on first use with cudaMalloc and released by qcams_shutdown().
+ *     on first use with cudaMalloc and released by qcams_shutdown(); make
+ *     the first call on a device before capturing any of its calls into a
+ *     CUDA graph.  Calls that use the context on one device (qcams_levels,
+ *     qcams_init_states, qcams_run_batch, qcams_analyze, qcams_autotune,
+ *     qcams_last_run_stats) share it: serialise them on one stream.
  *   - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default
  *     stream).  Calls only enqueue work on it and return without waiting,
  *     except where a function states that it synchronises.
@@ -31,8 +35,7 @@
  *     exception crosses the ABI.  Argument errors are detected before any
  *     work is enqueued.  Per-trajectory failures do not fail a call: they
  *     are reported in the lane status array.
- *   - Thread safety: calls on different streams may run concurrently; calls
- *     that share a batch must be ordered on one stream.
+ *   - Ordering: calls that share a batch must be ordered on one stream.
  */
 #ifndef QCAMS_H
 #define QCAMS_H
@@ -469,6 +472,31 @@ int qcams_sample_proposal(const qcams_proposal_spec* spec, const int64_t* qfix,
                           const int64_t* cdf, int64_t n, uint64_t seed, uint64_t id_offset,
                           double* b, double* const* u_out, double* w, int32_t* cell,
                           void* cuda_stream);
+
+/* ---------------------------------------------------------------------- */
+/* Reports derived from cross sections and histograms (host, synchronous). */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Rate constants k(E) = sigma(E) sqrt(2 E / mu123) (Sec. 4, Eq. 19, with the
+ * atom-molecule reduced mass mu123 for mu) and their standard errors, for n
+ * collision energies: host arrays sigma, sigma_se, E_col in; k, k_se out.
+ */
+int qcams_rate_constants(const double* sigma, const double* sigma_se, const double* E_col,
+                         int32_t n, double mu123, double* k, double* k_se);
+
+/*
+ * Gaussian-binned product vibrational distributions (Sec. 2.3, Eqs. 14-15)
+ * over the cells cell_ids[n_sel] of a host copy of the histograms
+ * hist[n_cells][QCAMS_H_STRIDE]: with S_c(v) the summed Gaussian weights of
+ * channel c in {Q, R_AC, R_BC} at v_t = v and N_D the dissociations,
+ * W = sum_v (S_Q(v) + S_RAC(v) + S_RBC(v)) + N_D and
+ * out[64 c + v] = S_c(v) / W (out: host double [3][64]; v = 63 collects
+ * v_t >= 63).  *W_out (optional) receives W.  Returns QCAMS_E_INVALID for
+ * an empty selection or W = 0.
+ */
+int qcams_gb_distribution(const int64_t* hist, int32_t n_cells, const int32_t* cell_ids,
+                          int32_t n_sel, double* out, double* W_out);
 
 /* ---------------------------------------------------------------------- */
 /* Measurement and housekeeping.                                           */

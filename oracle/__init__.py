@@ -121,6 +121,8 @@ def lib():
                                       C.c_void_p]),
             "oracle_reduce": (None, [C.c_int64, _I32, _I32, _I32, _D, _D, _I32, C.c_int32, _I64]),
             "oracle_xsec": (None, [_I64, C.c_int32, _D, _D, _I32, C.c_int32, C.c_int32, _D]),
+            "oracle_rates": (None, [_D, _D, C.c_int32, C.c_double, _D]),
+            "oracle_gb_distribution": (C.c_double, [_I64, _I32, C.c_int32, _D]),
             "oracle_mlp_num_params": (C.c_int, []),
             "oracle_mlp_forward": (None, [_D, _D, C.c_int64, _D]),
             "oracle_mlp_loss_grad": (C.c_double, [_D, _D, _I32, C.c_int64, _D]),
@@ -467,3 +469,18 @@ def proposal_grid(dims, b2_max, E, v, j, mean, std):
     lib().oracle_proposal_grid(_i32(dims), float(b2_max), float(E), int(v), int(j),
                                _d(_arr(mean, np.float64)), _d(_arr(std, np.float64)), _d(x))
     return x
+
+
+def rates(sigma, E, mu123):
+    sigma, E = _arr(sigma, np.float64), _arr(E, np.float64)
+    k = np.zeros(sigma.size)
+    lib().oracle_rates(_d(sigma), _d(E), sigma.size, float(mu123), _d(k))
+    return k
+
+
+def gb_distribution(hist, cells):
+    hist = np.ascontiguousarray(hist, np.int64)
+    cells = _arr(cells, np.int32)
+    out = np.zeros(3 * 64)
+    W = lib().oracle_gb_distribution(hist.ctypes.data_as(_I64), _i32(cells), cells.size, _d(out))
+    return out.reshape(3, 64), W

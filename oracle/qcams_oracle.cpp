@@ -1029,4 +1029,29 @@ void oracle_xsec(const int64_t* hist, int32_t n_cells, const double* cell_b,
   delete[] var;
 }
 
+// Rate constant of Sec. 4 (Eq. 19): k = sigma sqrt(2 E / mu), with mu the
+// atom-molecule reduced mass mu123 (reading of the unlabelled mu).
+void oracle_rates(const double* sigma, const double* E, int32_t n, double mu123, double* k) {
+  for (int i = 0; i < n; ++i) k[i] = sigma[i] * std::sqrt(2.0 * E[i] / mu123);
+}
+
+// Gaussian-binning product distributions, Sec. 2.3 (Eqs. 14-15): over the
+// selected cells, P_c(v_t) = sum_i W_c^i(v_t) / W with the total weight
+// W = sum over v_t of the reaction and quench weight sums plus N_d (each
+// dissociation weighs 1).  out[3][64] for c = Q, R_AC, R_BC; returns W.
+double oracle_gb_distribution(const int64_t* hist, const int32_t* cells, int32_t n_sel,
+                              double* out) {
+  double W = 0.0;
+  for (int k = 0; k < 3 * N_VT; ++k) out[k] = 0.0;
+  for (int s = 0; s < n_sel; ++s) {
+    const int64_t* H = hist + (int64_t)H_STRIDE * cells[s];
+    for (int c = 0; c < 3; ++c)
+      for (int v = 0; v < N_VT; ++v) out[N_VT * c + v] += std::ldexp(double(H[H_GB + N_VT * c + v]), -32);
+    W += double(H[H_COUNT + kClsD]);
+  }
+  for (int k = 0; k < 3 * N_VT; ++k) W += out[k];
+  for (int k = 0; k < 3 * N_VT; ++k) out[k] /= W;
+  return W;
+}
+
 }  // extern "C"

@@ -73,6 +73,8 @@ cudaError_t ctx_get(Ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->shapes, sizeof(DevShape) * QCAMS_MAX_SYS * 3);
   if (e == cudaSuccess) e = cudaMalloc(&c->levels, sizeof(DevLevel) * kLevelCells);
   if (e == cudaSuccess) e = cudaMalloc(&c->level_flag, kLevelCells);
+  if (e == cudaSuccess) e = cudaMalloc(&c->level_valid, kLevelCells);
+  if (e == cudaSuccess) e = cudaMemset(c->level_valid, 0, kLevelCells);
   if (e == cudaSuccess) e = cudaMalloc(&c->counters, sizeof(unsigned long long) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&c->req_out, sizeof(qcams_level) * kMaxLevelsReq);
   if (e == cudaSuccess) e = cudaMalloc(&c->req_in, sizeof(int32_t) * 3 * kMaxLevelsReq);
@@ -89,7 +91,7 @@ cudaError_t ctx_get(Ctx** out) {
   }
   if (e != cudaSuccess) {
     cudaFree(c->shapes); cudaFree(c->levels); cudaFree(c->level_flag); cudaFree(c->counters);
-    cudaFree(c->req_out); cudaFree(c->req_in);
+    cudaFree(c->req_out); cudaFree(c->req_in); cudaFree(c->level_valid);
     for (int k = 0; k < 4; ++k) if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
     return e;
@@ -460,19 +462,20 @@ __device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu,
   return L;
 }
 
-// Mark the (sys, v, j) levels the lanes need.
+// Mark the (sys, v, j) levels the lanes need and the cache does not hold.
 __global__ void k_mark_levels(int64_t n, const int32_t* sys_id, const int32_t* v,
-                              const int32_t* j, int n_sys, uint8_t* flag) {
+                              const int32_t* j, int n_sys, const uint8_t* valid, uint8_t* flag) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   int s = sys_id[i], vv = v[i], jj = j[i];
   if (s < 0 || s >= n_sys || vv < 0 || vv > QCAMS_V_MAX || jj < 0 || jj > QCAMS_J_MAX) return;
-  flag[level_index(s, vv, jj)] = 1;
+  const int idx = level_index(s, vv, jj);
+  if (!valid[idx]) flag[idx] = 1;
 }
 
 // Solve every marked level of the dense table (one thread per table cell).
 __global__ void k_solve_levels(SysSet sys, const DevShape* shapes, const uint8_t* flag,
-                               DevLevel* levels) {
+                               DevLevel* levels, uint8_t* valid) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= kLevelCells || !flag[idx]) return;
   int s = idx / (kLevelV * kLevelJ);
@@ -480,6 +483,7 @@ __global__ void k_solve_levels(SysSet sys, const DevShape* shapes, const uint8_t
   int j = idx % kLevelJ;
   if (s >= sys.n) return;
   levels[idx] = solve_level(sys.s[s].pair[0], shapes[s * 3], sys.s[s].mu_pair[0], v, j);
+  valid[idx] = 1;
 }
 
 // Levels for an explicit request list (qcams_levels).
@@ -593,7 +597,11 @@ __device__ PairBound pair_bound(const DevPair& q, const DevShape& sh, double mu,
                                 double E, double r) {
   PairBound pb{false, 0.0, INFINITY};
   double thr;
-  if (!sh.ok || !eff_well(q, sh, mu, L2, &pb.r_min, &pb.r_top, &thr)) return pb;
+  // The barrier top r_0 lies beyond r_peak where V < 0, so the threshold
+  // V_eff(r_0) is below L2 / (2 mu r_peak^2) (and is 0 for L2 = 0): a pair
+  // at or above that energy is unbound without any root search.
+  if (!sh.ok || E >= L2 / (2.0 * mu * sh.r_peak * sh.r_peak)) return pb;
+  if (!eff_well(q, sh, mu, L2, &pb.r_min, &pb.r_top, &thr)) return pb;
   bool b = E < thr && r < pb.r_top;
   if (q.kind == QCAMS_BUCK) b = b && r > sh.r_b && E < veff(q, mu, L2, sh.r_b);
   pb.bound = b;
@@ -923,11 +931,26 @@ int qcams_init_states(const qcams_system* sys, int32_t n_sys, const double* E_co
   const int64_t n = batch->n;
   const unsigned grid = (unsigned)((n + 255) / 256);
   k_pair_shapes<<<1, 32, 0, st>>>(ss, ctx->shapes);
-  cudaError_t e = cudaMemsetAsync(ctx->level_flag, 0, kLevelCells, st);
+  // Level cache: a system slot keeps its solved levels while its AB pair and
+  // masses are unchanged (the levels depend on nothing else).
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < n_sys && e == cudaSuccess; ++k) {
+    double key[9] = {sys[k].mass[0], sys[k].mass[1], (double)sys[k].pair[0].kind,
+                     sys[k].pair[0].p[0], sys[k].pair[0].p[1], sys[k].pair[0].p[2],
+                     sys[k].pair[0].p[3], sys[k].pair[0].p[4], 0.0};
+    if (!ctx->level_key_set[k] || std::memcmp(key, ctx->level_key[k], sizeof(key)) != 0) {
+      e = cudaMemsetAsync(ctx->level_valid + (size_t)k * kLevelV * kLevelJ, 0,
+                          (size_t)kLevelV * kLevelJ, st);
+      std::memcpy(ctx->level_key[k], key, sizeof(key));
+      ctx->level_key_set[k] = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->level_flag, 0, kLevelCells, st);
   if (e != cudaSuccess) return QCAMS_E_CUDA;
-  k_mark_levels<<<grid, 256, 0, st>>>(n, batch->sys_id, v, j, n_sys, ctx->level_flag);
+  k_mark_levels<<<grid, 256, 0, st>>>(n, batch->sys_id, v, j, n_sys, ctx->level_valid,
+                                      ctx->level_flag);
   k_solve_levels<<<(kLevelCells + 63) / 64, 64, 0, st>>>(ss, ctx->shapes, ctx->level_flag,
-                                                          ctx->levels);
+                                                          ctx->levels, ctx->level_valid);
   k_init<<<grid, 256, 0, st>>>(ss, ctx->levels, E_col, b, v, j, R0, seed, id_offset,
                                u_in ? u_in[0] : nullptr, u_in ? u_in[1] : nullptr,
                                u_in ? u_in[2] : nullptr, u_in ? u_in[3] : nullptr, d);
@@ -1063,6 +1086,42 @@ int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_
   for (int g = 0; g < ng; ++g)
     for (int k = 0; k < NE; ++k)
       grp[2 * NE * (size_t)g + 2 * k + 1] = 2.0 * kPi * std::sqrt(var[NE * (size_t)g + k]);
+  return QCAMS_OK;
+}
+
+int qcams_rate_constants(const double* sigma, const double* sigma_se, const double* E_col,
+                         int32_t n, double mu123, double* k, double* k_se) {
+  if (n < 0 || !finite_pos(mu123)) return QCAMS_E_INVALID;
+  if (n > 0 && (!sigma || !sigma_se || !E_col || !k || !k_se)) return QCAMS_E_INVALID;
+  for (int i = 0; i < n; ++i) {
+    if (!(E_col[i] >= 0.0)) return QCAMS_E_INVALID;
+    const double vrel = std::sqrt(2.0 * E_col[i] / mu123);
+    k[i] = sigma[i] * vrel;
+    k_se[i] = sigma_se[i] * vrel;
+  }
+  return QCAMS_OK;
+}
+
+int qcams_gb_distribution(const int64_t* hist, int32_t n_cells, const int32_t* cell_ids,
+                          int32_t n_sel, double* out, double* W_out) {
+  if (!hist || !cell_ids || !out || n_cells < 1 || n_sel < 1) return QCAMS_E_INVALID;
+  double S[3][64] = {};
+  double Nd = 0.0;
+  for (int s = 0; s < n_sel; ++s) {
+    const int c = cell_ids[s];
+    if (c < 0 || c >= n_cells) return QCAMS_E_INVALID;
+    const int64_t* h = hist + (size_t)c * QCAMS_H_STRIDE;
+    for (int ch = 0; ch < 3; ++ch)
+      for (int v = 0; v < 64; ++v) S[ch][v] += std::ldexp((double)h[QCAMS_H_GB + 64 * ch + v], -32);
+    Nd += (double)h[QCAMS_H_COUNT + QCAMS_CLS_D];
+  }
+  double W = Nd;
+  for (int ch = 0; ch < 3; ++ch)
+    for (int v = 0; v < 64; ++v) W += S[ch][v];
+  if (!(W > 0.0)) return QCAMS_E_INVALID;
+  for (int ch = 0; ch < 3; ++ch)
+    for (int v = 0; v < 64; ++v) out[64 * ch + v] = S[ch][v] / W;
+  if (W_out) *W_out = W;
   return QCAMS_OK;
 }
 
@@ -1210,7 +1269,7 @@ int qcams_shutdown(void) {
   if (!c) return QCAMS_OK;
   cudaDeviceSynchronize();
   cudaFree(c->shapes); cudaFree(c->levels); cudaFree(c->level_flag); cudaFree(c->counters);
-  cudaFree(c->req_out); cudaFree(c->req_in);
+  cudaFree(c->req_out); cudaFree(c->req_in); cudaFree(c->level_valid);
   for (int k = 0; k < 4; ++k) if (c->ev[k]) cudaEventDestroy(c->ev[k]);
   delete c;
   g_ctx[dev] = nullptr;

@@ -14,7 +14,12 @@ struct Ctx {
   int sm_count = 0;
   DevShape* shapes = nullptr;          // [QCAMS_MAX_SYS][3]
   DevLevel* levels = nullptr;          // [kLevelCells]
-  uint8_t* level_flag = nullptr;       // [kLevelCells]
+  uint8_t* level_flag = nullptr;       // [kLevelCells] levels to solve in this call
+  uint8_t* level_valid = nullptr;      // [kLevelCells] levels[] holds a solved level
+  // per system slot: the AB-pair parameters and masses the cached levels
+  // were solved for (levels depend on nothing else)
+  double level_key[QCAMS_MAX_SYS][9] = {};
+  bool level_key_set[QCAMS_MAX_SYS] = {};
   unsigned long long* counters = nullptr;  // [8]: 0 rhs, 1 steps, 2 queue head
   qcams_level* req_out = nullptr;      // [65536] qcams_levels output staging
   int32_t* req_in = nullptr;           // [3 * 65536] qcams_levels input staging

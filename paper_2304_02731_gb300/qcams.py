@@ -39,7 +39,7 @@ EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_i
            "qcams_debug_exp", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
            "qcams_mlp_features", "qcams_mlp_fit_standardizer", "qcams_mlp_grad",
            "qcams_mlp_train_step", "qcams_mlp_infer", "qcams_build_proposal",
-           "qcams_sample_proposal"]
+           "qcams_sample_proposal", "qcams_rate_constants", "qcams_gb_distribution"]
 MLP_NPARAMS = 9156
 
 
@@ -154,6 +154,8 @@ def lib():
                 "qcams_build_proposal": (C.c_int, [P(CMLP), P(ProposalSpec), V, V, V, V]),
                 "qcams_sample_proposal": (C.c_int, [P(ProposalSpec), V, V, I64, C.c_uint64,
                                                     C.c_uint64, V, V, V, V, V]),
+                "qcams_rate_constants": (C.c_int, [P(D), P(D), P(D), I32, D, P(D), P(D)]),
+                "qcams_gb_distribution": (C.c_int, [P(I64), I32, P(I32), I32, P(D), P(D)]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -577,3 +579,31 @@ def mlp_features(batch: Batch, E, b, v, j) -> torch.Tensor:
            "qcams_mlp_features")
     torch.cuda.current_stream().synchronize()
     return x
+
+
+# ---------------------------------------------------------------------------
+# reports
+# ---------------------------------------------------------------------------
+def rate_constants(sigma, sigma_se, E_col, mu123: float):
+    """qcams_rate_constants: (k, k_se) host arrays."""
+    sg, se, E = (np.ascontiguousarray(a, np.float64) for a in (sigma, sigma_se, E_col))
+    k, kse = np.zeros(sg.size), np.zeros(sg.size)
+    P = C.POINTER(C.c_double)
+    _check(lib().qcams_rate_constants(sg.ctypes.data_as(P), se.ctypes.data_as(P),
+                                      E.ctypes.data_as(P), sg.size, float(mu123),
+                                      k.ctypes.data_as(P), kse.ctypes.data_as(P)),
+           "qcams_rate_constants")
+    return k, kse
+
+
+def gb_distribution(hist, cell_ids):
+    """qcams_gb_distribution: ([3, 64] distribution, W) from host histograms."""
+    h = np.ascontiguousarray(np.asarray(hist).reshape(-1, H_STRIDE), np.int64)
+    ids = np.ascontiguousarray(cell_ids, np.int32)
+    out = np.zeros(3 * 64)
+    W = C.c_double()
+    _check(lib().qcams_gb_distribution(h.ctypes.data_as(C.POINTER(C.c_int64)), h.shape[0],
+                                       ids.ctypes.data_as(C.POINTER(C.c_int32)), ids.size,
+                                       out.ctypes.data_as(C.POINTER(C.c_double)), C.byref(W)),
+           "qcams_gb_distribution")
+    return out.reshape(3, 64), W.value

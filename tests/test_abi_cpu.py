@@ -103,3 +103,30 @@ def test_entry_points_reject_bad_arguments_without_a_device(Q):
     assert L.qcams_last_run_stats(None, None) == -1
     f = C.c_double()
     assert L.qcams_fma_peak(16, C.byref(f), None) == -1
+
+
+def test_rate_constants_match_oracle(Q, oracle):
+    from paper_2304_02731_gb300 import workloads as W
+    s = oracle.system_from_spec(W.SYS_H2_CA_MORSE)
+    mu = oracle.reduced_masses(s)["mu123"]
+    E = W.sweep_energies()
+    sig = np.linspace(1.0, 30.0, E.size)
+    k, kse = Q.rate_constants(sig, 0.1 * sig, E, mu)
+    ko = oracle.rates(sig, E, mu)
+    assert np.allclose(k, ko, rtol=1e-15) and np.allclose(kse, 0.1 * ko, rtol=1e-14)
+
+
+def test_gb_distribution_matches_oracle(Q, oracle):
+    rng = np.random.default_rng(6)
+    n = 5000
+    cls = rng.integers(0, 6, n)
+    vt = rng.integers(0, 70, n)
+    gbw = rng.uniform(0.0, 9.0, n)
+    cell = rng.integers(0, 5, n)
+    H = oracle.reduce(cls, vt, np.zeros(n, np.int32), gbw, cell, 5)
+    P, Wt = Q.gb_distribution(H, [1, 3, 4])
+    Po, Wo = oracle.gb_distribution(H, [1, 3, 4])
+    assert Wt == pytest.approx(Wo, rel=1e-15)
+    assert np.allclose(P, Po, rtol=1e-14, atol=0)
+    with pytest.raises(Q.QcamsError):
+        Q.gb_distribution(H, [])

@@ -619,3 +619,40 @@ def test_weighted_xsec_is_the_sample_mean_of_weighted_indicators(oracle):
         assert cells[0, k, 0] == pytest.approx(y.mean(), rel=1e-9)
         assert cells[0, k, 1] == pytest.approx(y.std(ddof=1) / math.sqrt(N), rel=1e-9)
         assert groups[0, k, 0] == pytest.approx(math.pi * 100.0 * y.mean(), rel=1e-9)
+
+
+def test_rate_is_sigma_times_initial_relative_speed(oracle):
+    """k = sigma sqrt(2 E / mu123) equals sigma times the speed at which the
+    atom approaches the molecule in the initial state (|d rho2 / dt|)."""
+    s = oracle.system_from_spec(W.SYS_H2_CA_MORSE)
+    mu = oracle.reduced_masses(s)["mu123"]
+    E = np.array([0.02, 0.1, 0.4])
+    st = oracle.init([s], np.zeros(3, np.int32), E, np.zeros(3), np.zeros(3, np.int32),
+                     np.zeros(3, np.int32), 30.0, 0)
+    speed = np.linalg.norm(st["y"][:, 9:12], axis=1) / mu
+    k = oracle.rates(np.array([2.0, 3.0, 5.0]), E, mu)
+    assert np.allclose(k, np.array([2.0, 3.0, 5.0]) * speed, rtol=1e-14)
+
+
+def test_gb_distribution_normalisation_and_integer_case(oracle):
+    """Eqs. 14-15: the channel distributions plus the dissociation share
+    N_d / W sum to one; when every v' is an integer each lane carries the peak
+    weight 1/(sigma sqrt(2 pi)), so P_c(v) = n_c(v) / (n_bound + N_d s sqrt(2 pi))."""
+    rng = np.random.default_rng(4)
+    n = 3000
+    cls = rng.choice(6, n, p=[0.5, 0.15, 0.15, 0.1, 0.05, 0.05])
+    vt = rng.integers(0, 12, n)
+    sig = 0.042466
+    peak = 1.0 / (sig * math.sqrt(2 * math.pi))
+    gbw = np.where(cls <= 2, peak, 0.0)
+    cell = rng.integers(0, 3, n)
+    H = oracle.reduce(cls, vt, np.zeros(n, np.int32), gbw, cell, 3)
+    P, Wt = oracle.gb_distribution(H, [0, 2])
+    sel = (cell == 0) | (cell == 2)
+    Nd = np.sum(sel & (cls == 3))
+    assert P.sum() + Nd / Wt == pytest.approx(1.0, rel=1e-12)
+    nb = np.sum(sel & (cls <= 2))
+    for c in range(3):
+        for v in range(12):
+            ncv = np.sum(sel & (cls == c) & (vt == v))
+            assert P[c, v] == pytest.approx(ncv / (nb + Nd / peak), rel=1e-9, abs=1e-15)
