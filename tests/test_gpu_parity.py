@@ -387,3 +387,18 @@ def test_fp32_kahan_integrator_against_fp64(Q, oracle):
     torch.cuda.synchronize()
     h0 = b0.host()
     assert np.all(h0["cls"][h0["status"] == 2] == 0)
+
+
+def test_gpu_levels_against_dvr(Q, oracle):
+    """Cross-check of the device Bohr-Sommerfeld levels with the paper's DVR
+    (oracle): within 0.5 % of the local vibrational spacing for j > 0."""
+    from oracle import dvr
+    s = oracle.system_from_spec(W.SYS_H2_CA_MORSE)
+    mu = oracle.reduced_masses(s)["mu12"]
+    cases = [(v, j) for j in (2, 9, 17) for v in (0, 4, 9)]
+    got = Q.levels([W.SYS_H2_CA_MORSE], np.zeros(len(cases), np.int32),
+                   [c[0] for c in cases], [c[1] for c in cases])
+    for k, (v, j) in enumerate(cases):
+        E = dvr.dvr_levels(s.pair[0], mu, j, 0.3, 14.0, 900)
+        assert got["ok"][k]
+        assert abs(got["E"][k] - E[v]) < 5e-3 * (E[v + 1] - E[v]), (v, j)
