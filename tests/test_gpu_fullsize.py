@@ -121,13 +121,13 @@ def _oracle_chunk(payload):
     return cls
 
 
-def test_full_size_cross_sections_within_3se_of_oracle(full_run, oracle):
-    """Every cross section of the full GPU sweep lies within 3 combined
-    standard errors of the oracle's estimate from 16 lanes per (E, b) cell
-    (6,144 trajectories run one by one, one oracle process per host core)."""
+@pytest.fixture(scope="module")
+def oracle_sample(full_run, oracle):
+    """The oracle's classes for 16 lanes per (E, b) cell of the sweep (6,144
+    trajectories run one by one, one oracle process per host core)."""
     import multiprocessing as mp
     import os
-    wl, out, hist, cells, groups = full_run
+    wl = full_run[0]
     idx = W.stratified(wl, 16)
     cores = max(1, min(os.cpu_count() or 1, 32))
     parts = [c for c in np.array_split(np.arange(len(idx)), cores) if len(c)]
@@ -135,6 +135,10 @@ def test_full_size_cross_sections_within_3se_of_oracle(full_run, oracle):
                  wl.j[idx[c]], wl.R0, wl.seed, idx[c], dict(wl.integ)) for c in parts]
     with mp.get_context("spawn").Pool(len(payloads)) as pool:
         cls_o = np.concatenate(pool.map(_oracle_chunk, payloads))
+    return idx, cls_o
+
+
+def _within_3se(wl, groups, idx, cls_o, oracle):
     zeros = np.zeros(len(idx), np.int32)
     h_o = oracle.reduce(cls_o, zeros, zeros, np.zeros(len(idx)), wl.cell[idx], wl.n_cells)
     _, g_o = oracle.xsec(h_o, wl.cell_b, wl.cell_w, wl.cell_group, wl.n_groups)
@@ -152,4 +156,39 @@ def test_full_size_cross_sections_within_3se_of_oracle(full_run, oracle):
             se = math.hypot(groups[g, k, 1], max(g_o[g, k, 1], se_o))
             worst = max(worst, d / se)
             assert d <= 3.0 * se, (g, k, groups[g, k], g_o[g, k])
+    return worst
+
+
+def test_full_size_cross_sections_within_3se_of_oracle(full_run, oracle_sample, oracle):
+    """Every cross section of the full GPU sweep lies within 3 combined
+    standard errors of the oracle's estimate from the sampled lanes."""
+    wl, out, hist, cells, groups = full_run
+    worst = _within_3se(wl, groups, *oracle_sample, oracle)
     print(f"\nlargest |sigma_gpu - sigma_oracle| / SE over 16 energies x 4 channels: {worst:.2f}")
+
+
+def test_fp32_full_size_against_fp64_oracle(full_run, oracle_sample, oracle):
+    """The FP32 integrator with compensated updates (tolerances 1e-6 / 1e-8)
+    on the same 3,145,728 trajectories: every cross section within 3 combined
+    standard errors of the FP64 oracle's; energy drift and class agreement
+    with the FP64 run are reported."""
+    import torch
+    from paper_2304_02731_gb300 import qcams as Q
+    wl = full_run[0]
+    integ = Q.make_integ(**W.INTEG_FP32, persistent=True, precision=32)
+    b32, hist32, cells32, groups32 = Q.run_workload(wl, integ)
+    torch.cuda.synchronize()
+    st = Q.last_run_stats()
+    worst = _within_3se(wl, groups32, *oracle_sample, oracle)
+    cls32, status32 = b32.cls.cpu().numpy(), b32.status.cpu().numpy()
+    dE, E0 = b32.f64["dE"].cpu().numpy(), b32.f64["E0"].cpu().numpy()
+    sep = status32 == 2
+    rel = np.abs(dE[sep]) / np.maximum(np.abs(E0[sep]), wl.E[sep])
+    out64 = full_run[1]
+    done = sep & (out64["status"] == 2)
+    agree = np.mean(cls32[done] == out64["cls"][done])
+    print(f"\nFP32: worst sigma deviation {worst:.2f} SE; |dE/E| median {np.median(rel):.2e} "
+          f"99% {np.quantile(rel, .99):.2e}; class agreement with FP64 {agree:.4f} over "
+          f"{done.sum()} lanes; integrator {st['integrate_ms']:.1f} ms")
+    assert np.all(np.isin(status32, [2, 3]))
+    assert agree > 0.99 and np.median(rel) < 1e-5
