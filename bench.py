@@ -36,6 +36,11 @@ if ROOT not in sys.path:
 # (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 594 DFMA,
 # 212 DMUL, 19 DADD per lane-step, six right-hand sides included.
 FP64_FLOP_PER_STEP = 1419
+# FP32 floating-point operations per attempted step of the FP32 Morse kernel
+# (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
+# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 506 FFMA,
+# 216 FMUL, 57 FADD per lane-step); it also issues one DADD (the time).
+FP32_FLOP_PER_STEP = 1286
 # DRAM bytes per trajectory of the integrator (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum on the profile case, 686,080 B for 3,840 lanes; the
 # state is loaded once and stored once, everything else is in registers).
@@ -69,7 +74,7 @@ def parse():
                     help="pick the launch shape with qcams_autotune before timing")
     ap.add_argument("--graph", type=int, default=1,
                     help="capture the step (init, run, reduce) in a CUDA graph")
-    ap.add_argument("--cpu-per-cell", type=int, default=8,
+    ap.add_argument("--cpu-per-cell", type=int, default=32,
                     help="oracle sample for cpu_baseline: lanes per cell")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -313,13 +318,14 @@ def run_ours(args):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    integ_ms, steps_total, rhs_total = [], 0, 0
+    integ_ms, analyze_ms, steps_total, rhs_total = [], [], 0, 0
     stream = torch.cuda.current_stream()
     e0.record(stream)
     for _ in range(args.steps):
         run_step()
         st = Q.last_run_stats()          # synchronises; read after each step's run
         integ_ms.append(st["integrate_ms"])
+        analyze_ms.append(st["analyze_ms"])
         steps_total += st["steps"]
         rhs_total += st["rhs"]
     e1.record(stream)
@@ -363,22 +369,26 @@ def run_ours(args):
         e2e = {"value": world * wl.n * args.steps / wall, "unit": "trajectories/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hhist.numel() * 8)}
 
-    # roofline of the dominant kernel (the integrator): FP64 pipe
-    fp64_peak = Q.fma_peak(64)          # measured here: MEASURED_PEAKS.json has no FP64 figure
+    # roofline of the dominant kernel (the integrator): the FP64 pipe for
+    # the FP64 kernel, the FP32 FMA pipe for the FP32 one
+    peak = Q.fma_peak(args.precision)    # measured here: MEASURED_PEAKS.json has no FP64/FP32 figure
     avg_integ_ms = float(np.mean(integ_ms))
     steps_per_launch = steps_total / max(1, args.steps)
-    roofline = {"bound": "alu", "unit": "TFLOP/s",
-                "peak": fp64_peak / 1e12,
-                "peak_source": "measured DFMA chain microbenchmark (qcams_fma_peak), this run",
+    flop_per_step = FP64_FLOP_PER_STEP if args.precision == 64 else FP32_FLOP_PER_STEP
+    roofline = {"bound": "alu", "unit": "TFLOP/s", "peak": peak / 1e12,
+                "peak_source": f"measured FP{args.precision} FMA-chain microbenchmark "
+                               f"(qcams_fma_peak), this run",
                 "traffic": DRAM_BYTES_PER_LANE * wl.n if args.workload == "sweep" else None,
                 "traffic_note": "ncu dram bytes of the 3,840-lane profile case scaled by lanes"}
-    if FP64_FLOP_PER_STEP and args.precision == 64:
-        ach = FP64_FLOP_PER_STEP * steps_per_launch / (avg_integ_ms * 1e-3)
-        roofline.update(achieved=ach / 1e12, frac=ach / fp64_peak,
-                        flop_per_step=FP64_FLOP_PER_STEP)
+    if args.workload in ("sweep", "plain"):
+        # FLOP counts are those of the Morse kernel (H2 + Ca systems)
+        ach = flop_per_step * steps_per_launch / (avg_integ_ms * 1e-3)
+        roofline.update(achieved=ach / 1e12, frac=ach / peak, flop_per_step=flop_per_step)
     else:
         roofline.update(achieved=None, frac=None)
     roofline.update(steps_per_launch=steps_per_launch, integrate_ms=avg_integ_ms,
+                    analyze_ms=float(np.mean(analyze_ms)),
+                    rest_of_step_ms=ms_max / args.steps - avg_integ_ms,
                     rhs_per_launch=rhs_total / max(1, args.steps))
 
     cpu = None
@@ -386,7 +396,9 @@ def run_ours(args):
         r, cores, n, wall = oracle_rate(wl, args.cpu_per_cell)
         cpu = {"value": r, "unit": "trajectories/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} lanes ({args.cpu_per_cell} per (E, b) cell), {wall:.1f} s wall "
-                         f"on {cores} host cores"}
+                         f"on {cores} host cores",
+               "seconds_per_trajectory_one_core": cores * wall / max(n, 1),
+               "one_core_trajectories_per_s": n / (cores * wall)}
 
     cls_counts = np.bincount(hb["cls"], minlength=6).tolist()
     line = {

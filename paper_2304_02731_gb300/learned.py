@@ -79,9 +79,13 @@ def train(mlp: "Q.MLP", x: torch.Tensor, cls: torch.Tensor, epochs: int = 8,
     return losses
 
 
-def best_state(host, min_count: int = 200):
-    """(v, j) with the largest reactive fraction in the training data."""
+def best_state(host, min_count: int | None = None):
+    """(v, j) with the largest reactive fraction in the training data, among
+    the states holding at least min_count lanes (default: 200, or half the
+    mean count per state when the data are smaller)."""
     v, j, cls = host["v"], host["j"], host["cls"]
+    if min_count is None:
+        min_count = min(200, max(1, len(cls) // (2 * 11 * 21)))
     key = v * 21 + j
     n = np.bincount(key, minlength=11 * 21)
     r = np.bincount(key, weights=((cls == 1) | (cls == 2)).astype(float), minlength=11 * 21)
