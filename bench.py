@@ -33,9 +33,13 @@ if ROOT not in sys.path:
 
 # FP64 floating-point operations per attempted integrator step of the Morse
 # kernel: 2 dfma + dmul + dadd, from ncu sass counters on the profile case
-# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 594 DFMA,
-# 212 DMUL, 19 DADD per lane-step, six right-hand sides included.
-FP64_FLOP_PER_STEP = 1419
+# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 540 DFMA,
+# 230 DMUL, 19 DADD per lane-step, six right-hand sides included.  The FP64
+# pipe issues 540 + 230 + 19 = 789 instructions per step; the DFMA-chain
+# peak runs one DFMA (2 FLOP) per pipe slot, so pipe_frac below is the
+# fraction of the pipe's instruction rate the kernel uses.
+FP64_FLOP_PER_STEP = 1329
+FP64_INSTR_PER_STEP = 789
 # FP32 floating-point operations per attempted step of the FP32 Morse kernel
 # (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
 # profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 506 FFMA,
@@ -384,6 +388,9 @@ def run_ours(args):
         # FLOP counts are those of the Morse kernel (H2 + Ca systems)
         ach = flop_per_step * steps_per_launch / (avg_integ_ms * 1e-3)
         roofline.update(achieved=ach / 1e12, frac=ach / peak, flop_per_step=flop_per_step)
+        if args.precision == 64:
+            rate = FP64_INSTR_PER_STEP * steps_per_launch / (avg_integ_ms * 1e-3)
+            roofline.update(fp64_instr_per_step=FP64_INSTR_PER_STEP, pipe_frac=rate / (peak / 2))
     else:
         roofline.update(achieved=None, frac=None)
     roofline.update(steps_per_launch=steps_per_launch, integrate_ms=avg_integ_ms,

@@ -14,6 +14,7 @@
 #include "qcams.h"
 #include "qcams_device.cuh"
 #include "qcams_internal.h"
+#include "texp.cuh"
 
 namespace qcams {
 namespace {
@@ -24,38 +25,15 @@ constexpr int kMaxDevices = 64;
 constexpr int kMaxLevelsReq = 65536;
 constexpr int kMaxCells = 65536;
 
-// Gauss-Legendre rules on [-1, 1] (positive half of the symmetric nodes):
-// 64 points for the per-lane action integral, 128 for the level solver.
+// Gauss-Legendre rules in the sine-mapped variable (positive half of the
+// symmetric nodes, written by gen_gl_tables.py): 64 points for the per-lane
+// action integral, 128 for the level solver.  Compile-time constants, so
+// every entry point can use them without a context.
 constexpr int kGL64 = 64, kGL128 = 128;
-__constant__ double cGL64x[kGL64 / 2], cGL64w[kGL64 / 2];
-__constant__ double cGL128x[kGL128 / 2], cGL128w[kGL128 / 2];
+#include "gl_tables.inc"
 
 std::mutex g_mutex;
 Ctx* g_ctx[kMaxDevices] = {nullptr};
-
-// Gauss-Legendre nodes and weights by Newton iteration on P_n(x), with the
-// three-term recurrence for P_n and the derivative identity
-// (x^2 - 1) P_n' = n (x P_n - P_{n-1}); w = 2 / ((1 - x^2) P_n'^2).
-void gauss_legendre(int n, double* x_pos, double* w_pos) {
-  for (int i = 0; i < n / 2; ++i) {
-    double x = std::cos(kPi * (i + 0.75) / (n + 0.5));
-    double dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = x;
-      for (int k = 2; k <= n; ++k) {
-        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-        p0 = p1;
-        p1 = p2;
-      }
-      dp = n * (x * p1 - p0) / (x * x - 1.0);
-      double dx = p1 / dp;
-      x -= dx;
-      if (std::fabs(dx) < 1e-16) break;
-    }
-    x_pos[i] = x;
-    w_pos[i] = 2.0 / ((1.0 - x * x) * dp * dp);
-  }
-}
 
 cudaError_t ctx_get(Ctx** out) {
   int dev = 0;
@@ -80,15 +58,6 @@ cudaError_t ctx_get(Ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->req_in, sizeof(int32_t) * 3 * kMaxLevelsReq);
   if (e == cudaSuccess) e = cudaMemset(c->counters, 0, sizeof(unsigned long long) * 8);
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
-  if (e == cudaSuccess) {
-    double x64[kGL64 / 2], w64[kGL64 / 2], x128[kGL128 / 2], w128[kGL128 / 2];
-    gauss_legendre(kGL64, x64, w64);
-    gauss_legendre(kGL128, x128, w128);
-    e = cudaMemcpyToSymbol(cGL64x, x64, sizeof(x64));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGL64w, w64, sizeof(w64));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGL128x, x128, sizeof(x128));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGL128w, w128, sizeof(w128));
-  }
   if (e != cudaSuccess) {
     cudaFree(c->shapes); cudaFree(c->levels); cudaFree(c->level_flag); cudaFree(c->counters);
     cudaFree(c->req_out); cudaFree(c->req_in); cudaFree(c->level_valid);
@@ -152,7 +121,8 @@ int make_devpair(const qcams_pair& in, DevPair* out) {
 }
 
 int make_sysset(const qcams_system* sys, int32_t n_sys, SysSet* out) {
-  if (!sys || n_sys < 1 || n_sys > QCAMS_MAX_SYS) return QCAMS_E_INVALID;
+  if (!sys || n_sys < 1) return QCAMS_E_INVALID;
+  if (n_sys > QCAMS_MAX_SYS) return QCAMS_E_CAPACITY;
   std::memset(out, 0, sizeof(*out));
   out->n = n_sys;
   for (int s = 0; s < n_sys; ++s) {
@@ -317,21 +287,54 @@ __global__ void k_pair_shapes(SysSet sys, DevShape* out) {
   out[t] = pair_shape(sys.s[t / 3].pair[t % 3]);
 }
 
-// Well of the effective potential V + L2/(2 mu r^2): bottom r_min and outer
-// maximum r_top (r_top = +inf and threshold 0 when L2 = 0).  Returns false
-// when L2/mu >= g_max (no well).
-__device__ bool eff_well(const DevPair& q, const DevShape& sh, double mu, double L2,
-                         double* r_min, double* r_top, double* thr) {
+// Potentials with the exponential taken either from CUDA's exp (TAB =
+// false: level solver) or from the shared-memory table T (TAB = true:
+// product analysis, one table-driven exp per evaluation).
+template <bool TAB>
+__device__ __forceinline__ double pot_V_(const DevPair& q, double r, const double* T) {
+  if (!TAB || q.kind == QCAMS_LJ) return pot_V(q, r);
+  if (q.kind == QCAMS_MORSE) {
+    const double u = 1.0 - texp(q.c1 - q.c0 * r, T);
+    return q.c3 * u * u - q.c3;
+  }
+  const double ri = 1.0 / r, ri2 = ri * ri;
+  return q.c0 * texp(-q.c1 * r, T) - q.c4 * ri2 * ri2 * ri2;
+}
+template <bool TAB>
+__device__ __forceinline__ double pot_dV_(const DevPair& q, double r, const double* T) {
+  if (!TAB || q.kind == QCAMS_LJ) return pot_dV(q, r);
+  if (q.kind == QCAMS_MORSE) {
+    const double x = texp(q.c1 - q.c0 * r, T);
+    return q.c2 * x * (1.0 - x);
+  }
+  const double ri = 1.0 / r, ri2 = ri * ri;
+  return q.c3 * ri2 * ri2 * ri2 * ri - q.c2 * texp(-q.c1 * r, T);
+}
+template <bool TAB>
+__device__ __forceinline__ double veff_(const DevPair& q, double mu, double L2, double r,
+                                        const double* T) {
+  return pot_V_<TAB>(q, r, T) + L2 / (2.0 * mu * r * r);
+}
+template <bool TAB>
+__device__ __forceinline__ double gfun_(const DevPair& q, double r, const double* T) {
+  return r * r * r * pot_dV_<TAB>(q, r, T);
+}
+
+// Outer barrier of the effective potential V + L2/(2 mu r^2): the root
+// r_top > r_peak of g(r) = L2/mu and the threshold V_eff(r_top).  r_top =
+// +inf and threshold 0 when L2 = 0 or when the barrier lies beyond reach.
+// Returns false when L2/mu >= g_max (no well).
+template <bool TAB>
+__device__ bool barrier_top(const DevPair& q, const DevShape& sh, double mu, double L2,
+                            const double* T, double* r_top, double* thr) {
   if (L2 <= 0.0) {
-    *r_min = sh.r_eq;
     *r_top = INFINITY;
     *thr = 0.0;
     return true;
   }
   const double c = L2 / mu;
   if (!(c < sh.g_max)) return false;
-  auto G = [&](double r) { return gfun(q, r) - c; };
-  *r_min = illinois(G, sh.r_eq, sh.r_peak, -c, sh.g_max - c);
+  auto G = [&](double r) { return gfun_<TAB>(q, r, T) - c; };
   double a = sh.r_peak, b = 2.0 * sh.r_peak, gb = G(b);
   for (int it = 0; it < 60 && gb >= 0.0; ++it) {
     a = b;
@@ -344,16 +347,36 @@ __device__ bool eff_well(const DevPair& q, const DevShape& sh, double mu, double
     return true;
   }
   *r_top = illinois(G, a, b, G(a), gb);
-  *thr = veff(q, mu, L2, *r_top);
+  *thr = veff_<TAB>(q, mu, L2, *r_top, T);
   return true;
 }
 
-// Turning points of E = V_eff inside the well.
+// Well of the effective potential: bottom r_min and outer barrier (r_top,
+// threshold).  Returns false when L2/mu >= g_max (no well).
+__device__ bool eff_well(const DevPair& q, const DevShape& sh, double mu, double L2,
+                         double* r_min, double* r_top, double* thr) {
+  if (!barrier_top<false>(q, sh, mu, L2, nullptr, r_top, thr)) return false;
+  if (L2 <= 0.0) {
+    *r_min = sh.r_eq;
+    return true;
+  }
+  const double c = L2 / mu;
+  auto G = [&](double r) { return gfun(q, r) - c; };
+  *r_min = illinois(G, sh.r_eq, sh.r_peak, -c, sh.g_max - c);
+  return true;
+}
+
+// Turning points of E = V_eff inside the well, bracketed by a split point
+// r_in of the classically allowed region (V_eff(r_in) < E: the well bottom
+// for the level solver, the pair's own separation in the analysis) and the
+// barrier top.
+template <bool TAB>
 __device__ bool turning_points(const DevPair& q, const DevShape& sh, double mu, double L2, double E,
-                               double r_min, double r_top, double* rm, double* rp) {
-  auto f = [&](double r) { return veff(q, mu, L2, r) - E; };
-  double fmin_ = f(r_min);
-  if (!(fmin_ < 0.0)) return false;
+                               double r_in, double r_top, const double* T, double* rm,
+                               double* rp) {
+  auto f = [&](double r) { return veff_<TAB>(q, mu, L2, r, T) - E; };
+  double fin = f(r_in);
+  if (!(fin < 0.0)) return false;
   // inner: V_eff rises steeply toward small r (Buckingham: up to r_b)
   double lo, flo;
   if (q.kind == QCAMS_BUCK) {
@@ -361,7 +384,7 @@ __device__ bool turning_points(const DevPair& q, const DevShape& sh, double mu, 
     flo = f(lo);
     if (!(flo > 0.0)) return false;
   } else {
-    lo = 0.5 * r_min;
+    lo = 0.5 * r_in;
     flo = f(lo);
     for (int it = 0; it < 60 && flo <= 0.0; ++it) {
       lo *= 0.5;
@@ -369,13 +392,13 @@ __device__ bool turning_points(const DevPair& q, const DevShape& sh, double mu, 
     }
     if (!(flo > 0.0)) return false;
   }
-  *rm = illinois(f, lo, r_min, flo, fmin_);
+  *rm = illinois(f, lo, r_in, flo, fin);
   double hi, fhi;
   if (isfinite(r_top)) {
     hi = r_top;
     fhi = f(hi);
   } else {
-    hi = 2.0 * r_min;
+    hi = 2.0 * r_in;
     fhi = f(hi);
     for (int it = 0; it < 60 && fhi <= 0.0; ++it) {
       hi *= 2.0;
@@ -383,36 +406,39 @@ __device__ bool turning_points(const DevPair& q, const DevShape& sh, double mu, 
     }
   }
   if (!(fhi > 0.0)) return false;
-  *rp = illinois(f, r_min, hi, fmin_, fhi);
+  *rp = illinois(f, r_in, hi, fin, fhi);
   return true;
 }
 
 // Action and period integrals by Gauss-Legendre in s after r = c + d sin(s)
 // (the mapped integrands are smooth on the closed interval):
 //   I_act = int sqrt(E - V_eff) dr,  I_per = int dr / sqrt(E - V_eff).
-template <int NG>
+// The node sines and the weights times the map's cosine are tabulated.
+// PERIOD = false skips the period sum (the product analysis needs only the
+// action).
+template <int NG, bool TAB, bool PERIOD>
 __device__ void action_period(const DevPair& q, double mu, double L2, double E, double rm,
-                              double rp, double* act, double* per) {
+                              double rp, const double* T, double* act, double* per) {
   const double c = 0.5 * (rp + rm), d = 0.5 * (rp - rm);
+  const double a = L2 / (2.0 * mu);
   double sa = 0.0, sp = 0.0;
+#pragma unroll 4
   for (int k = 0; k < NG / 2; ++k) {
-    const double x = (NG == kGL64) ? cGL64x[k] : cGL128x[k];
-    const double w = (NG == kGL64) ? cGL64w[k] : cGL128w[k];
-    double sn, cs;
-    sincospi(0.5 * x, &sn, &cs);
+    const double sn = (NG == kGL64) ? kGL64S[k] : kGL128S[k];
+    const double wc = (NG == kGL64) ? kGL64WC[k] : kGL128WC[k];
 #pragma unroll
     for (int sgn = 0; sgn < 2; ++sgn) {
-      const double r = sgn ? c - d * sn : c + d * sn;
-      const double g = E - veff(q, mu, L2, r);
+      const double r = sgn ? fma(-d, sn, c) : fma(d, sn, c);
+      const double g = E - (pot_V_<TAB>(q, r, T) + a / (r * r));
       if (g > 0.0) {
         const double sq = sqrt(g);
-        sa += w * sq * d * cs;
-        sp += w * d * cs / sq;
+        sa = fma(wc, sq, sa);
+        if (PERIOD) sp += wc / sq;
       }
     }
   }
-  *act = 0.5 * kPi * sa;
-  *per = 0.5 * kPi * sp;
+  *act = 0.5 * kPi * d * sa;
+  if (PERIOD) *per = 0.5 * kPi * d * sp;
 }
 
 // Bohr-Sommerfeld level: solve v(E) = -1/2 + sqrt(2 mu)/pi I_act(E) = v by a
@@ -429,8 +455,8 @@ __device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu,
   const double s2mu = sqrt(2.0 * mu);
   double lo = Vmin, hi = Etop - 1e-10 * (Etop - Vmin);
   double rm, rp, act, per;
-  if (!turning_points(q, sh, mu, L2, hi, r_min, r_top, &rm, &rp)) return L;
-  action_period<kGL128>(q, mu, L2, hi, rm, rp, &act, &per);
+  if (!turning_points<false>(q, sh, mu, L2, hi, r_min, r_top, nullptr, &rm, &rp)) return L;
+  action_period<kGL128, false, true>(q, mu, L2, hi, rm, rp, nullptr, &act, &per);
   if (-0.5 + s2mu / kPi * act < v) return L;
   // harmonic first guess
   double k2 = pot_d2V(q, r_min) + 3.0 * L2 / (mu * r_min * r_min * r_min * r_min);
@@ -438,8 +464,8 @@ __device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu,
   if (!(E > lo && E < hi)) E = 0.5 * (lo + hi);
   bool ok = false;
   for (int it = 0; it < 200; ++it) {
-    if (!turning_points(q, sh, mu, L2, E, r_min, r_top, &rm, &rp)) break;
-    action_period<kGL128>(q, mu, L2, E, rm, rp, &act, &per);
+    if (!turning_points<false>(q, sh, mu, L2, E, r_min, r_top, nullptr, &rm, &rp)) break;
+    action_period<kGL128, false, true>(q, mu, L2, E, rm, rp, nullptr, &act, &per);
     const double f = -0.5 + s2mu / kPi * act - v;
     if (f < 0) lo = E; else hi = E;
     double En = E - f * 2.0 * kPi / (s2mu * per);
@@ -452,8 +478,8 @@ __device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu,
     E = En;
   }
   if (!ok) return L;
-  if (!turning_points(q, sh, mu, L2, E, r_min, r_top, &rm, &rp)) return L;
-  action_period<kGL128>(q, mu, L2, E, rm, rp, &act, &per);
+  if (!turning_points<false>(q, sh, mu, L2, E, r_min, r_top, nullptr, &rm, &rp)) return L;
+  action_period<kGL128, false, true>(q, mu, L2, E, rm, rp, nullptr, &act, &per);
   L.E = E;
   L.r_minus = rm;
   L.r_plus = rp;
@@ -588,85 +614,118 @@ __global__ void k_init(SysSet sys, const DevLevel* levels, const double* E_col, 
 // ---------------------------------------------------------------------------
 // Product analysis (Sec. 2.2).
 // ---------------------------------------------------------------------------
-struct PairBound {
-  bool bound;
-  double r_min, r_top;
-};
-
-__device__ PairBound pair_bound(const DevPair& q, const DevShape& sh, double mu, double L2,
-                                double E, double r) {
-  PairBound pb{false, 0.0, INFINITY};
+// Bound test of one pair (Sec. 2.2 with reading R13): E below the barrier
+// threshold V_eff(r_top) and the pair inside its barrier (r < r_top; for
+// Buckingham also outside the short-range maximum, r > r_b, and E below
+// V_eff(r_b)).  Sets r_top for the turning-point search.  Two exact
+// shortcuts skip the root search for unbound pairs:
+//  * the barrier top lies beyond r_peak, where V < 0, so the threshold is
+//    below L2/(2 mu r_peak^2): a pair at or above that energy is unbound;
+//  * beyond r_peak, g(r) = r^3 V'(r) decreases through L2/mu exactly at
+//    r_top (g is unimodal there), so g(r) < L2/mu at r > r_peak means
+//    r > r_top: the pair is outside its barrier.
+__device__ bool pair_bound(const DevPair& q, const DevShape& sh, double mu, double L2, double E,
+                           double r, const double* T, double* r_top) {
+  *r_top = INFINITY;
+  if (!sh.ok || E >= L2 / (2.0 * mu * sh.r_peak * sh.r_peak)) return false;
+  if (!(L2 / mu < sh.g_max)) return false;
+  if (r > sh.r_peak && gfun_<true>(q, r, T) < L2 / mu) return false;
   double thr;
-  // The barrier top r_0 lies beyond r_peak where V < 0, so the threshold
-  // V_eff(r_0) is below L2 / (2 mu r_peak^2) (and is 0 for L2 = 0): a pair
-  // at or above that energy is unbound without any root search.
-  if (!sh.ok || E >= L2 / (2.0 * mu * sh.r_peak * sh.r_peak)) return pb;
-  if (!eff_well(q, sh, mu, L2, &pb.r_min, &pb.r_top, &thr)) return pb;
-  bool b = E < thr && r < pb.r_top;
-  if (q.kind == QCAMS_BUCK) b = b && r > sh.r_b && E < veff(q, mu, L2, sh.r_b);
-  pb.bound = b;
-  return pb;
+  if (!barrier_top<true>(q, sh, mu, L2, T, r_top, &thr)) return false;
+  bool b = E < thr && r < *r_top;
+  if (q.kind == QCAMS_BUCK) b = b && r > sh.r_b && E < veff_<true>(q, mu, L2, sh.r_b, T);
+  return b;
 }
 
-__global__ void k_analyze(SysSet sys, const DevShape* shapes, double gb_sigma, DevBatch B) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// Product analysis of lane i: energy error, arrangement class by the unique
+// bound pair, j' from its angular momentum, v' from its action (Eq. 10), the
+// integer bins and the Gaussian-binning weight (Sec. 2.2-2.3).
+__global__ void __launch_bounds__(128) k_analyze(SysSet sys, const DevShape* shapes,
+                                                 double gb_sigma, DevBatch B) {
+  __shared__ double sT[kExpTableSize];
+  load_exp_table(sT);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= B.n) return;
   const int st = B.status[i];
   const int sid = B.sys_id[i];
-  double y[12];
-  for (int k = 0; k < 12; ++k) y[k] = B.y[k][i];
   int cls = QCAMS_CLS_FAIL;
   double vp = 0.0, jp = 0.0, w = 0.0, dE = 0.0;
   int vt = 0, jt = 0;
-  if (sid >= 0 && sid < sys.n && st != QCAMS_LANE_NO_LEVEL && st != QCAMS_LANE_INVALID)
-    dE = hamiltonian(sys.s[sid], y) - B.E0[i];
-  if ((st == QCAMS_LANE_DONE_RSTOP || st == QCAMS_LANE_DONE_TMAX) && sid >= 0 && sid < sys.n) {
+  if (sid >= 0 && sid < sys.n && st != QCAMS_LANE_NO_LEVEL && st != QCAMS_LANE_INVALID) {
     const DevSys& S = sys.s[sid];
-    double r[3][3], vv[3][3];
-    for (int a = 0; a < 3; ++a) {
-      const double v1 = y[6 + a] * S.inv_mu12, v2 = y[9 + a] * S.inv_mu123;
-      r[0][a] = y[a];
-      r[1][a] = y[3 + a] - S.cB * y[a];
-      r[2][a] = y[3 + a] + S.cA * y[a];
-      vv[0][a] = v1;
-      vv[1][a] = v2 - S.cB * v1;
-      vv[2][a] = v2 + S.cA * v1;
-    }
-    int nb = 0, which = -1;
-    double Ep[3], L2p[3];
-    PairBound pbs[3];
+    double y[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) y[k] = B.y[k][i];
+    // pair separations, energies and squared angular momenta; their
+    // potentials also give the total energy (Eq. 2)
+    double d[3], Ep[3], L2p[3], Vsum = 0.0;
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const double mu = S.mu_pair[k];
-      const double d = sqrt(r[k][0] * r[k][0] + r[k][1] * r[k][1] + r[k][2] * r[k][2]);
-      const double v2 = vv[k][0] * vv[k][0] + vv[k][1] * vv[k][1] + vv[k][2] * vv[k][2];
-      const double Lx = r[k][1] * vv[k][2] - r[k][2] * vv[k][1];
-      const double Ly = r[k][2] * vv[k][0] - r[k][0] * vv[k][2];
-      const double Lz = r[k][0] * vv[k][1] - r[k][1] * vv[k][0];
-      Ep[k] = 0.5 * mu * v2 + pot_V(S.pair[k], d);
-      L2p[k] = mu * mu * (Lx * Lx + Ly * Ly + Lz * Lz);
-      pbs[k] = pair_bound(S.pair[k], shapes[sid * 3 + k], mu, L2p[k], Ep[k], d);
-      if (pbs[k].bound) { ++nb; which = k; }
-    }
-    if (nb == 0) cls = QCAMS_CLS_D;
-    else if (nb > 1) cls = QCAMS_CLS_AMBIG;
-    else {
-      cls = which == 0 ? QCAMS_CLS_Q : which == 2 ? QCAMS_CLS_R_AC : QCAMS_CLS_R_BC;
-      const DevPair& q = S.pair[which];
-      const DevShape& sh = shapes[sid * 3 + which];
-      const double mu = S.mu_pair[which];
-      double rm, rp, act, per;
-      vp = -0.5;
-      if (turning_points(q, sh, mu, L2p[which], Ep[which], pbs[which].r_min, pbs[which].r_top,
-                         &rm, &rp)) {
-        action_period<kGL64>(q, mu, L2p[which], Ep[which], rm, rp, &act, &per);
-        vp = -0.5 + sqrt(2.0 * mu) / kPi * act;
+      const double ck = k == 0 ? 0.0 : (k == 1 ? -S.cB : S.cA);
+      const double fk = k == 0 ? 0.0 : 1.0;
+      double r[3], v[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double v1 = y[6 + a] * S.inv_mu12, v2 = y[9 + a] * S.inv_mu123;
+        r[a] = k == 0 ? y[a] : fma(ck, y[a], y[3 + a]);
+        v[a] = k == 0 ? v1 : fma(ck, v1, fk * v2);
       }
-      jp = -0.5 + 0.5 * sqrt(1.0 + 4.0 * L2p[which]);
-      vt = (int)floor(vp + 0.5);
-      if (vt < 0) vt = 0;
-      jt = (int)floor(jp + 0.5);
-      const double dv = vp - vt;
-      w = exp(-dv * dv / (2.0 * gb_sigma * gb_sigma)) / (gb_sigma * sqrt(2.0 * kPi));
+      const double mu = S.mu_pair[k];
+      d[k] = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      const double V = pot_V_<true>(S.pair[k], d[k], sT);
+      Vsum += V;
+      const double Lx = r[1] * v[2] - r[2] * v[1];
+      const double Ly = r[2] * v[0] - r[0] * v[2];
+      const double Lz = r[0] * v[1] - r[1] * v[0];
+      Ep[k] = 0.5 * mu * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) + V;
+      L2p[k] = mu * mu * (Lx * Lx + Ly * Ly + Lz * Lz);
+    }
+    const double Tkin = (y[6] * y[6] + y[7] * y[7] + y[8] * y[8]) * (0.5 * S.inv_mu12) +
+                        (y[9] * y[9] + y[10] * y[10] + y[11] * y[11]) * (0.5 * S.inv_mu123);
+    dE = (Tkin + Vsum) - B.E0[i];
+    if (st == QCAMS_LANE_DONE_RSTOP || st == QCAMS_LANE_DONE_TMAX) {
+      bool bd[3];
+      double rtop[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        bd[k] = pair_bound(S.pair[k], shapes[sid * 3 + k], S.mu_pair[k], L2p[k], Ep[k], d[k], sT,
+                           &rtop[k]);
+      const int nb = (int)bd[0] + (int)bd[1] + (int)bd[2];
+      if (nb == 0) {
+        cls = QCAMS_CLS_D;
+      } else if (nb > 1) {
+        cls = QCAMS_CLS_AMBIG;
+      } else {
+        // the bound pair's quantities by selects (no dynamic register indexing)
+        const int which = bd[0] ? 0 : (bd[1] ? 1 : 2);
+        cls = which == 0 ? QCAMS_CLS_Q : which == 2 ? QCAMS_CLS_R_AC : QCAMS_CLS_R_BC;
+        const double E = bd[0] ? Ep[0] : (bd[1] ? Ep[1] : Ep[2]);
+        const double L2 = bd[0] ? L2p[0] : (bd[1] ? L2p[1] : L2p[2]);
+        const double r = bd[0] ? d[0] : (bd[1] ? d[1] : d[2]);
+        const double r_top = bd[0] ? rtop[0] : (bd[1] ? rtop[1] : rtop[2]);
+        const double mu = S.mu_pair[which];
+        const DevPair& q = S.pair[which];
+        const DevShape sh = shapes[sid * 3 + which];
+        double r_in = r;
+        if (!(veff_<true>(q, mu, L2, r, sT) < E)) {
+          // at a turning point within rounding: split at the well bottom
+          double rmin, rt, thr;
+          if (!eff_well(q, sh, mu, L2, &rmin, &rt, &thr)) rmin = sh.r_eq;
+          r_in = rmin;
+        }
+        double rm, rp, act, per;
+        vp = -0.5;
+        if (turning_points<true>(q, sh, mu, L2, E, r_in, r_top, sT, &rm, &rp)) {
+          action_period<kGL64, true, false>(q, mu, L2, E, rm, rp, sT, &act, &per);
+          vp = -0.5 + sqrt(2.0 * mu) / kPi * act;
+        }
+        jp = -0.5 + 0.5 * sqrt(1.0 + 4.0 * L2);
+        vt = (int)floor(vp + 0.5);
+        if (vt < 0) vt = 0;
+        jt = (int)floor(jp + 0.5);
+        const double dv = vp - vt;
+        w = exp(-dv * dv / (2.0 * gb_sigma * gb_sigma)) / (gb_sigma * sqrt(2.0 * kPi));
+      }
     }
   }
   B.cls[i] = (uint8_t)cls;

@@ -27,39 +27,16 @@
 //    leading mantissa bits, ratios in FP32), the stop tests (integer compares
 //    of non-negative doubles) and the minimum-step test (exponent compare).
 //  * The Morse exponential is a table-driven exponential (Tang's method) with
-//    a 256-entry table of 2^(j/256) in shared memory: 10 FP64 instructions.
+//    a 2048-entry table of 2^(j/2048) in shared memory: 8 FP64 instructions.
 #include <cuda_runtime.h>
 
 #include "qcams_device.cuh"
 #include "qcams_internal.h"
 #include "dp5_tableau.cuh"
+#include "texp.cuh"
 
 namespace qcams {
 namespace {
-
-#include "exp2_table.inc"
-
-// e^x by Tang's table-driven method (P. T. P. Tang, ACM Trans. Math. Softw.
-// 15 (1989) 144-157): x = (256 m + j) ln2/256 + r with |r| <= ln2/512, then
-// e^x = 2^m 2^(j/256) e^r with e^r - 1 from its degree-4 Taylor polynomial
-// (truncation < 4e-17 relative).  Arguments below -700 are clamped (e^-700 is
-// ~1e-304, far below any force term); the caller guarantees x < 700.
-__device__ __forceinline__ double texp(double x, const double* __restrict__ T) {
-  const double kShift = 6755399441055744.0;  // 1.5 * 2^52: rounds to an integer
-  x = fmax(x, -700.0);
-  const double t = fma(x, kExpInvL, kShift);
-  const int k = __double2loint(t);
-  const double kd = t - kShift;
-  double r = fma(-kd, kExpL1, x);
-  r = fma(-kd, kExpL2, r);
-  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
-  q = fma(q, r, 0.5);
-  q = q * r;
-  const double p = fma(q, r, r);
-  const double Tj = T[k & 255];
-  const double y = fma(Tj, p, Tj);
-  return __hiloint2double(__double2hiint(y) + ((k >> 8) << 20), __double2loint(y));
-}
 
 // |x| as a float, truncated to 20 mantissa bits, using only integer
 // instructions on the high word of x; values below 2^-126 become 0 and
@@ -140,17 +117,22 @@ __device__ __forceinline__ void stage_x(const double* rho, const double* vel, co
   const double hc = h * kT.c[s];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    double sum = 0.0;
+    if (s == 2) {
+      x[i] = fma(hc, vel[i], rho[i]);   // (A^2)_{2q} = 0: no acceleration term
+    } else {
+      double sum = kT.a2[s][1] * acc[0][i];
 #pragma unroll
-    for (int q = 1; q <= s - 2; ++q) sum = fma(kT.a2[s][q], acc[q - 1][i], sum);
-    x[i] = fma(hh, sum, fma(hc, vel[i], rho[i]));
+      for (int q = 2; q <= s - 2; ++q) sum = fma(kT.a2[s][q], acc[q - 1][i], sum);
+      x[i] = fma(hh, sum, fma(hc, vel[i], rho[i]));
+    }
   }
 }
 
 // One Dormand-Prince step of size h from (rho, vel) with acc[0] = a(rho).
 // On return acc[1..6] hold the stage accelerations, xn / vn the 5th-order
 // solution (acc[6] = a(xn), FSAL), er / ev the embedded error estimates of
-// positions and velocities, s2 the squared pair distances at xn.
+// positions and velocities divided by h^2 and h (the error norm applies
+// those factors in FP32), s2 the squared pair distances at xn.
 template <bool MORSE>
 __device__ __forceinline__ void dp_step(const DevSys& S, const double* __restrict__ T,
                                         const double* rho, const double* vel, double (*acc)[6],
@@ -179,11 +161,11 @@ __device__ __forceinline__ void dp_step(const DevSys& S, const double* __restric
     double e = kT.e[1] * acc[0][i];
 #pragma unroll
     for (int q = 3; q <= 7; ++q) e = fma(kT.e[q], acc[q - 1][i], e);
-    ev[i] = h * e;
+    ev[i] = e;
     double ea = kT.ea[1] * acc[0][i];
 #pragma unroll
     for (int q = 2; q <= 6; ++q) ea = fma(kT.ea[q], acc[q - 1][i], ea);
-    er[i] = hh * ea;
+    er[i] = ea;
   }
 }
 
@@ -329,14 +311,15 @@ __device__ __forceinline__ void lane_attempt(const SysSet& sys, const DevShape* 
   float sum = 0.f;
   const float rt = ip.rtol_f, at = ip.atol_f;
   const float atv0 = L.atv[0], atv1 = L.atv[1];
+  const float hf = mag_f(L.h, ignore), hhf = hf * hf;   // h > 0
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const float scr = fmaf(rt, fmaxf(mag_f(L.rho[i], ignore), mag_f(xn[i], ignore)), at);
-    const float qr = __fdividef(mag_f(er[i], bad), scr);
+    const float qr = __fdividef(mag_f(er[i], bad) * hhf, scr);
     sum = fmaf(qr, qr, sum);
     const float scv = fmaf(rt, fmaxf(mag_f(L.vel[i], ignore), mag_f(vn[i], ignore)),
                            i < 3 ? atv0 : atv1);
-    const float qv = __fdividef(mag_f(ev[i], bad), scv);
+    const float qv = __fdividef(mag_f(ev[i], bad) * hf, scv);
     sum = fmaf(qv, qv, sum);
   }
   const float en2 = sum * (1.0f / 12.0f);
@@ -397,18 +380,12 @@ __device__ __forceinline__ void flush_counters(unsigned long long rhs, unsigned 
   }
 }
 
-// Stage the exponential table in shared memory (2 KB per block).
-__device__ __forceinline__ void load_exp_table(double* sT) {
-  for (int k = threadIdx.x; k < 256; k += blockDim.x) sT[k] = kExp2Table[k];
-  __syncthreads();
-}
-
 // One thread per trajectory.
 template <bool MORSE, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_integrate_plain(SysSet sys, const DevShape* shapes,
                                                          IntegParams ip, DevBatch B,
                                                          unsigned long long* counters) {
-  __shared__ double sT[256];
+  __shared__ double sT[kExpTableSize];
   load_exp_table(sT);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long rhs = 0, steps = 0;
@@ -428,7 +405,7 @@ template <bool MORSE, int BLOCK, int MINB>
 __global__ void __launch_bounds__(BLOCK, MINB) k_integrate_persistent(SysSet sys, const DevShape* shapes,
                                                               IntegParams ip, DevBatch B,
                                                               unsigned long long* counters) {
-  __shared__ double sT[256];
+  __shared__ double sT[kExpTableSize];
   load_exp_table(sT);
   const unsigned lane = threadIdx.x & 31u;
   unsigned long long rhs = 0, steps = 0;
@@ -472,7 +449,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_integrate_persistent(SysSet sys
 template <bool MORSE>
 __global__ void __launch_bounds__(128) k_integrate_fixed(SysSet sys, IntegParams ip, DevBatch B,
                                                          unsigned long long* counters) {
-  __shared__ double sT[256];
+  __shared__ double sT[kExpTableSize];
   load_exp_table(sT);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long rhs = 0, steps = 0;
@@ -520,7 +497,7 @@ __global__ void __launch_bounds__(128) k_integrate_fixed(SysSet sys, IntegParams
 }
 
 __global__ void k_exp_check(const double* x, double* mine, double* ref, long long n) {
-  __shared__ double sT[256];
+  __shared__ double sT[kExpTableSize];
   load_exp_table(sT);
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;

@@ -140,14 +140,19 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
   {                                                                                  \
     const float hc = h * kTf.c[sIdx];                                                \
     _Pragma("unroll") for (int i = 0; i < 6; ++i) {                                  \
-      float sum = 0.0f;                                                              \
-      _Pragma("unroll") for (int q = 1; q <= (sIdx) - 2; ++q)                        \
+      float sum = kTf.a2[sIdx][1] * L.acc[0][i];                                     \
+      _Pragma("unroll") for (int q = 2; q <= (sIdx) - 2; ++q)                        \
           sum = fmaf(kTf.a2[sIdx][q], L.acc[q - 1][i], sum);                         \
       x[i] = fmaf(hh, sum, fmaf(hc, L.vel[i], L.rho[i]));                            \
     }                                                                                \
     accel<MORSE>(S, x, L.acc[(sIdx) - 1], s2);                                       \
   }
-  QCAMS_STAGE(2)
+  {  // stage 2: (A^2)_{2q} = 0, no acceleration term
+    const float hc = h * kTf.c[2];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x[i] = fmaf(hc, L.vel[i], L.rho[i]);
+    accel<MORSE>(S, x, L.acc[1], s2);
+  }
   QCAMS_STAGE(3)
   QCAMS_STAGE(4)
   QCAMS_STAGE(5)
