@@ -244,7 +244,8 @@ int qcams_levels(const qcams_system* sys, int32_t n_sys, const int32_t* sys_id,
  * unless u_in is given: then u_in[k][i] (device, 4 arrays of n) are used
  * (importance sampling).  Writes y, t = 0, h = 0, t_scale, E0, Ecol,
  * status (READY, NO_LEVEL or INVALID) and, if non-NULL, u[k].
- * Limits: 1 <= n_sys <= QCAMS_MAX_SYS; R0 > 0.  Lanes with v > QCAMS_V_MAX
+ * Limits: 1 <= n_sys <= QCAMS_MAX_SYS (more: QCAMS_E_CAPACITY, as for every
+ * entry point taking a system list); R0 > 0.  Lanes with v > QCAMS_V_MAX
  * or j > QCAMS_J_MAX get NO_LEVEL.  Asynchronous.
  */
 int qcams_init_states(const qcams_system* sys, int32_t n_sys, const double* E_col,

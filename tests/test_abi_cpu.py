@@ -82,7 +82,10 @@ def test_entry_points_reject_bad_arguments_without_a_device(Q):
     b.n = 10                      # all pointers NULL
     assert L.qcams_run_batch(sysarr, 1, C.byref(integ), C.byref(b), None) == -1
     assert L.qcams_run_batch(sysarr, 0, C.byref(integ), C.byref(b), None) == -1
-    assert L.qcams_run_batch(sysarr, 5, C.byref(integ), C.byref(b), None) == -1
+    # more systems than QCAMS_MAX_SYS: a size limit, rejected before any read
+    assert L.qcams_run_batch(sysarr, 5, C.byref(integ), C.byref(b), None) == -4
+    assert L.qcams_init_states(sysarr, 5, None, None, None, None, 30.0, 0, 0, None,
+                               C.byref(b), None) == -4
     assert L.qcams_run_batch(sysarr, 1, None, C.byref(b), None) == -1
     bad = Q.make_integ(rtol=-1.0)
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1

@@ -258,6 +258,69 @@ def test_empty_and_invalid_lanes(Q):
     assert list(batch.cls.cpu().numpy()) == [0, 5, 5, 5, 5]
 
 
+HEAVY_MORSE = dict(mass_u=(126.904, 126.904, 40.078),
+                   pairs=(("morse", 0.057, 5.0, 0.95), W.CAH_MORSE, W.CAH_MORSE))
+
+
+def test_table_edges_and_size_limits(Q, oracle):
+    """Maximum sizes.  The largest (v, j) the level table serves (QCAMS_V_MAX
+    = 63, QCAMS_J_MAX = 255) on a deep, heavy Morse molecule (about 120
+    bound levels) against the oracle, in the level solver and in the initial
+    states; (v, j) beyond the table give NO_LEVEL; QCAMS_MAX_SYS = 4 systems
+    in one call; the largest cell count (65,536) reduces bit-exactly and one
+    more cell is rejected as a capacity error."""
+    import torch
+    cases = [(63, 255), (63, 0), (0, 255), (40, 128)]
+    v = [c[0] for c in cases]
+    j = [c[1] for c in cases]
+    got = Q.levels([HEAVY_MORSE], np.zeros(len(cases), np.int32), v, j)
+    s = oracle.system_from_spec(HEAVY_MORSE)
+    mu = oracle.reduced_masses(s)["mu12"]
+    for k, (vv, jj) in enumerate(cases):
+        L = oracle.level(s.pair[0], mu, vv, jj)
+        assert L.ok and got["ok"][k], (vv, jj)
+        assert abs(got["E"][k] - L.E) <= 1e-12 * abs(L.E), (vv, jj, got["E"][k], L.E)
+        assert abs(got["r_plus"][k] - L.r_plus) <= 1e-11 * L.r_plus, (vv, jj)
+        assert abs(got["tau"][k] - L.tau) <= 1e-9 * L.tau, (vv, jj)
+    specs = [HEAVY_MORSE, W.SYS_H2_CA_MORSE, W.SYS_H2_CA_LJ12, W.SYS_H2_CA_BUCK]
+    sid = np.array([0, 0, 0, 0, 0, 1, 2, 3], np.int32)
+    vv = np.array([63, 63, 0, 64, 0, 0, 3, 1], np.int32)
+    jj = np.array([255, 0, 255, 0, 256, 0, 5, 2], np.int32)
+    E = np.full(8, 0.1)
+    b = np.full(8, 2.0)
+    batch, g, o = _init_both(Q, oracle, specs, E, b, vv, jj, sid, seed=3)
+    beyond = np.array([False, False, False, True, True, False, False, False])
+    assert np.all(g["status"][beyond] == Q.LANE["NO_LEVEL"])
+    ok = ~beyond
+    assert np.all(g["status"][ok] == 0) and np.all(o["status"][ok] == 0)
+    assert np.array_equal(g["u"][ok], o["u"][ok])
+    assert np.max(np.abs(g["y"][ok] - o["y"][ok]) / (np.abs(o["y"][ok]) + 1.0)) < 1e-11
+    with pytest.raises(Q.QcamsError) as err:
+        Q.init_states(specs + [W.SYS_H2_CA_LJ8], batch, E, b, vv, jj, 30.0, 3)
+    assert err.value.code == -4
+    # the largest cell count, every cell hit, unsorted
+    rng = np.random.default_rng(17)
+    nc = 65536
+    n = 3 * nc
+    cell = rng.permutation(np.arange(n) % nc)
+    big = Q.Batch.empty(n, "cuda", cell=cell)
+    cls = rng.integers(0, 6, n)
+    vt = rng.integers(0, 70, n)
+    jt = rng.integers(0, 300, n)
+    gbw = rng.uniform(0.0, 9.4, n)
+    big.cls.copy_(torch.as_tensor(cls, dtype=torch.uint8))
+    big.vt.copy_(torch.as_tensor(vt, dtype=torch.int16))
+    big.jt.copy_(torch.as_tensor(jt, dtype=torch.int16))
+    big.f64["gbw"].copy_(torch.as_tensor(gbw))
+    hist, _, _ = Q.reduce_xsec(big, nc, finalize=False)
+    torch.cuda.synchronize()
+    ho = oracle.reduce(cls, vt, jt, gbw, cell, nc)
+    assert np.array_equal(hist.cpu().numpy(), ho)
+    with pytest.raises(Q.QcamsError) as err:
+        Q.reduce_xsec(big, nc + 1, finalize=False)
+    assert err.value.code == -4
+
+
 def test_mixed_potentials_parity(Q, oracle):
     """Buckingham / LJ(12,6) / LJ(8,6) Ca-H with mixed (v, j): outcome classes
     agree for >= 99% of lanes."""
@@ -387,6 +450,34 @@ def test_fp32_kahan_integrator_against_fp64(Q, oracle):
     torch.cuda.synchronize()
     h0 = b0.host()
     assert np.all(h0["cls"][h0["status"] == 2] == 0)
+
+
+def test_fp32_integrator_on_lj_and_buckingham(Q):
+    """The FP32 integrator's generic (non-Morse) force path: mixed-study lanes
+    over Buckingham, LJ(12,6) and LJ(8,6) Ca-H against the FP64 path on the
+    same lanes.  No lane fails numerically, the energy drift stays at the
+    FP32 tolerance level and the outcome classes agree on >= 95 % of the
+    lanes that reached a product in both runs."""
+    import torch
+    wl = W.mixed_ca_h(n=3000, seed=11)
+    res = {}
+    for prec, kw in [(64, W.INTEG_FP64), (32, W.INTEG_FP32)]:
+        integ = Q.make_integ(**kw, persistent=True, precision=prec)
+        b, _, _, _ = Q.run_workload(wl, integ)
+        torch.cuda.synchronize()
+        res[prec] = b.host()
+    h64, h32 = res[64], res[32]
+    assert not np.any(np.isin(h32["status"], [Q.LANE["FAIL_NAN"], Q.LANE["FAIL_HMIN"]]))
+    assert np.array_equal(h32["status"] == Q.LANE["NO_LEVEL"], h64["status"] == Q.LANE["NO_LEVEL"])
+    sep = h32["status"] == Q.LANE["DONE_RSTOP"]
+    rel = np.abs(h32["dE"][sep]) / np.maximum(np.abs(h32["E0"][sep]), wl.E[sep])
+    done = sep & (h64["status"] == Q.LANE["DONE_RSTOP"])
+    agree = np.mean(h32["cls"][done] == h64["cls"][done])
+    print(f"\nFP32 mixed potentials: median |dE/E| {np.median(rel):.2e}; class agreement "
+          f"{agree:.4f} over {done.sum()} lanes")
+    assert done.sum() > 0.6 * wl.n
+    assert np.median(rel) < 1e-5
+    assert agree >= 0.95
 
 
 def test_gpu_levels_against_dvr(Q, oracle):

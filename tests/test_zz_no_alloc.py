@@ -6,6 +6,10 @@ table and counters) is rewritten and cleared between calls.  The same
 lanes give bit-identical results, which satisfies any tolerance the other
 parity tests use."""
 import ctypes as C
+import os
+import subprocess
+import sys
+import textwrap
 
 import numpy as np
 import pytest
@@ -64,3 +68,50 @@ def test_noalloc_rejects_too_many_systems(Q):
     integ = Q.make_integ()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     assert Q.lib().qcams_run_batch_noalloc(arr, 5, C.byref(integ), C.byref(batch.c), stream) == -4
+
+
+_CHILD = textwrap.dedent("""
+    import ctypes as C, sys
+    import numpy as np, torch
+    sys.path.insert(0, sys.argv[1])
+    from paper_2304_02731_gb300 import qcams as Q
+    from paper_2304_02731_gb300 import workloads as W
+    src = np.load(sys.argv[2])
+    wl = W.plain_h2_ca(per_b=12)
+    batch = Q.Batch.empty(wl.n, "cuda", sys_id=wl.sys_id, cell=wl.cell)
+    batch.y.copy_(torch.as_tensor(src["y0"]))
+    for k in Q._FIELDS_F64:
+        batch.f64[k].copy_(torch.as_tensor(src["f0_" + k]))
+    batch.status.copy_(torch.as_tensor(src["status0"]))
+    integ = Q.make_integ(**wl.integ, persistent=True)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = Q.lib().qcams_run_batch_noalloc(Q.systems_array(wl.systems), len(wl.systems),
+                                         C.byref(integ), C.byref(batch.c), stream)
+    assert rc == 0, rc
+    torch.cuda.synchronize()
+    np.savez(sys.argv[3], **batch.host())
+""")
+
+
+def test_noalloc_as_the_first_call_of_a_process(Q, tmp_path):
+    """In a fresh process whose only library call is qcams_run_batch_noalloc
+    (no per-device context exists), the results equal qcams_run_batch's on
+    the same initial states."""
+    import torch
+    wl = W.plain_h2_ca(per_b=12)
+    batch = Q.Batch.empty(wl.n, "cuda", sys_id=wl.sys_id, cell=wl.cell)
+    Q.init_states(wl.systems, batch, wl.E, wl.b, wl.v, wl.j, wl.R0, wl.seed, wl.id_offset)
+    torch.cuda.synchronize()
+    init = {"y0": batch.y.cpu().numpy(), "status0": batch.status.cpu().numpy()}
+    init.update({"f0_" + k: v.cpu().numpy() for k, v in batch.f64.items()})
+    np.savez(tmp_path / "init.npz", **init)
+    Q.run_batch(wl.systems, batch, Q.make_integ(**wl.integ, persistent=True))
+    torch.cuda.synchronize()
+    ref = batch.host()
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([sys.executable, "-c", _CHILD, root, str(tmp_path / "init.npz"),
+                    str(tmp_path / "out.npz")], check=True, timeout=600)
+    got = np.load(tmp_path / "out.npz")
+    assert np.all(np.isin(got["status"], [2, 3])), got["status"]
+    for k in FIELDS:
+        assert np.array_equal(got[k], ref[k]), k
