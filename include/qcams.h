@@ -436,6 +436,20 @@ int qcams_mlp_grad(const qcams_mlp* m, const float* x, const uint8_t* cls, int64
  * eps 1e-8, bias-corrected) with learning rate lr; increments m->step. */
 int qcams_mlp_train_step(qcams_mlp* m, const float* x, const uint8_t* cls, int64_t n,
                          float lr, float* loss_out, void* cuda_stream);
+/*
+ * `steps` minibatch Adam steps on the samples (x[n][8], cls[n]) as
+ * qcams_mlp_train_step takes them, all on the device: before each step the
+ * batch row indices idx[0..batch) (caller-owned device int64 scratch) are
+ * drawn uniformly on [0, n) with replacement (Philox4x32-10, key = seed,
+ * counter (i, step_lo, step_hi, 4) with step = m->step before the update;
+ * index = high 64 bits of (w1:w0) * n), the gradient is taken over the
+ * gathered rows and Adam updates the parameters.  losses (device float
+ * [steps], optional) receives each step's minibatch loss.  On return idx
+ * holds the last step's indices.  Asynchronous; capturable in a graph.
+ */
+int qcams_mlp_train(qcams_mlp* m, const float* x, const uint8_t* cls, int64_t n, int64_t steps,
+                    int32_t batch, float lr, uint64_t seed, int64_t* idx, float* losses,
+                    void* cuda_stream);
 /* Class probabilities probs[n][4] (device float) for inputs x[n][8]. */
 int qcams_mlp_infer(const qcams_mlp* m, const float* x, int64_t n, float* probs,
                     void* cuda_stream);
@@ -449,7 +463,8 @@ int qcams_mlp_infer(const qcams_mlp* m, const float* x, int64_t n, float* probs,
  * (defensive mixture: q_c >= alpha / N, so every weight is <= 1 / alpha).
  * q (device double [N]); qfix (device int64 [N]) = round(q 2^40) and
  * cdf (device int64 [N]) its inclusive prefix sums: sampling uses the exact
- * integer distribution qfix / cdf[N-1].  N <= 2^22.  Asynchronous.
+ * integer distribution qfix / cdf[N-1].  N <= 2^22 (more: QCAMS_E_CAPACITY).
+ * Asynchronous.
  */
 typedef struct {
   double E_col;

@@ -41,22 +41,25 @@ struct Std {
 
 // Shared-memory weight tiles (BF16).  Forward B operands use W as [N][K];
 // backward dA = dZ W needs W^T as [K][N].  Padding: W1 K 8 -> 16, W4 N 4 -> 8
-// (forward) and W4^T N 4 -> 16.
+// (forward) and W4^T N 4 -> 16.  Every row is padded by 8 elements (16 B):
+// a fragment load touches rows g = 0..7 at words 2q / 2 + const, and the
+// 16-byte row skew puts the 8 rows x 4 words on 32 distinct banks.
+constexpr int PK = 8;   // row padding (BF16 elements)
 struct WeightsSmem {
-  __nv_bfloat16 w1[H][16];
-  __nv_bfloat16 w2[H][H];
-  __nv_bfloat16 w3[H][H];
-  __nv_bfloat16 w4[8][H];
-  __nv_bfloat16 w2t[H][H];
-  __nv_bfloat16 w3t[H][H];
-  __nv_bfloat16 w4t[H][16];
+  __nv_bfloat16 w1[H][16 + PK];
+  __nv_bfloat16 w2[H][H + PK];
+  __nv_bfloat16 w3[H][H + PK];
+  __nv_bfloat16 w4[8][H + PK];
+  __nv_bfloat16 w2t[H][H + PK];
+  __nv_bfloat16 w3t[H][H + PK];
+  __nv_bfloat16 w4t[H][16 + PK];
   float b1[H], b2[H], b3[H], b4[8];
 };
 struct WarpSmem {
-  float z[3][32][32];          // pre-activations of layers 1-3, fragment order [i][lane]
-  __nv_bfloat16 xt[16][16];    // X^T  [feature (padded)][sample]
-  __nv_bfloat16 at[3][H][16];  // A1^T, A2^T, A3^T [unit][sample]
-  __nv_bfloat16 dzt[H][16];    // dZ^T [unit][sample]
+  float z[3][32][32];               // pre-activations of layers 1-3, fragment order [i][lane]
+  __nv_bfloat16 xt[16][16 + PK];    // X^T  [feature (padded)][sample]
+  __nv_bfloat16 at[3][H][16 + PK];  // A1^T, A2^T, A3^T [unit][sample]
+  __nv_bfloat16 dzt[H][16 + PK];    // dZ^T [unit][sample]
 };
 struct TrainSmem {
   WeightsSmem w;
@@ -123,14 +126,15 @@ struct CellGrid {
   int n_b2, n_cth, n_phi, n_eta, n_chi;
   float E, v, j, b2_max;
 };
-__device__ __forceinline__ void features(const float* x, int64_t n, int64_t row,
-                                         const CellGrid* grid, float* f) {
+__device__ __forceinline__ void features(const float* x, const int64_t* idx, int64_t n,
+                                         int64_t row, const CellGrid* grid, float* f) {
   if (row >= n) {
     for (int k = 0; k < IN; ++k) f[k] = 0.0f;
     return;
   }
   if (!grid) {
-    for (int k = 0; k < IN; ++k) f[k] = x[row * IN + k];
+    const int64_t r = idx ? idx[row] : row;   // minibatch rows gathered through idx
+    for (int k = 0; k < IN; ++k) f[k] = x[r * IN + k];
     return;
   }
   int64_t c = row;
@@ -154,12 +158,13 @@ __device__ __forceinline__ void features(const float* x, int64_t n, int64_t row,
 // With TRAIN, pre-activations and transposed activations are kept in the
 // warp's shared tiles for the backward pass.
 template <bool TRAIN>
-__device__ void forward16(const WeightsSmem& W, WarpSmem* ws, const float* x, int64_t n,
-                          int64_t base, const CellGrid* grid, const Std& sd, float* logit) {
+__device__ void forward16(const WeightsSmem& W, WarpSmem* ws, const float* x, const int64_t* idx,
+                          int64_t n, int64_t base, const CellGrid* grid, const Std& sd,
+                          float* logit) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   float f0[IN], f1[IN];
-  features(x, n, base + g, grid, f0);
-  features(x, n, base + g + 8, grid, f1);
+  features(x, idx, n, base + g, grid, f0);
+  features(x, idx, n, base + g + 8, grid, f1);
   for (int k = 0; k < IN; ++k) {
     f0[k] = (f0[k] - sd.mean[k]) * sd.inv_std[k];
     f1[k] = (f1[k] - sd.mean[k]) * sd.inv_std[k];
@@ -246,7 +251,7 @@ __device__ __forceinline__ void softmax_pair(float z0, float z1, float* p0, floa
 
 // dW (+)= dZ^T A for one layer: M = n_out (16-row tiles), K = 16 samples,
 // N = n_in (8-column tiles), into the CTA gradient accumulator.
-__device__ void accumulate_dw(const WarpSmem* ws, const __nv_bfloat16 (*aT)[16], int m_tiles,
+__device__ void accumulate_dw(const WarpSmem* ws, const __nv_bfloat16 (*aT)[16 + PK], int m_tiles,
                               int n_tiles, int n_out_valid, int n_in, float* gW) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   for (int mt = 0; mt < m_tiles; ++mt) {
@@ -302,17 +307,19 @@ __device__ __forceinline__ void accumulate_db(const float (*dz)[4], int tiles, i
   }
 }
 
+// Gradient of the mean cross-entropy over n rows; with idx, row r of the
+// minibatch is sample idx[r] of (x, label).
 __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, const float* pf,
                                                       Std sd, const float* x,
-                                                      const uint8_t* label, int64_t n,
-                                                      float* grad, float* loss) {
+                                                      const uint8_t* label, const int64_t* idx,
+                                                      int64_t n, float* grad, float* loss) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   load_weights(S.w, pb, pf);
   for (int i = threadIdx.x; i < NP; i += blockDim.x) S.grad[i] = 0.0f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   WarpSmem* ws = &S.warp[warp];
-  for (int i = lane; i < H * 16; i += 32) (&ws->dzt[0][0])[i] = __float2bfloat16(0.0f);
+  for (int i = lane; i < H * (16 + PK); i += 32) (&ws->dzt[0][0])[i] = __float2bfloat16(0.0f);
   __syncthreads();
   const float inv_n = 1.0f / (float)n;
   float loss_acc = 0.0f;
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
        ch += (int64_t)gridDim.x * WARPS) {
     const int64_t base = ch * 16;
     float lg[4];
-    forward16<true>(S.w, ws, x, n, base, nullptr, sd, lg);
+    forward16<true>(S.w, ws, x, idx, n, base, nullptr, sd, lg);
     // softmax cross-entropy and dZ4 = (p - onehot) / n
     float dz4[1][4] = {{0.f, 0.f, 0.f, 0.f}};
     float p[4];
@@ -329,7 +336,8 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
     softmax_pair(lg[2], lg[3], &p[2], &p[3]);
     if (q < 2) {
       const int64_t r0 = base + g, r1 = base + g + 8;
-      int l0 = r0 < n ? (int)label[r0] : -1, l1 = r1 < n ? (int)label[r1] : -1;
+      int l0 = r0 < n ? (int)label[idx ? idx[r0] : r0] : -1;
+      int l1 = r1 < n ? (int)label[idx ? idx[r1] : r1] : -1;
       if (l0 >= OUT) l0 = -1;   // AMBIG / FAIL lanes carry no target
       if (l1 >= OUT) l1 = -1;
       for (int e = 0; e < 2; ++e) {
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_infer(const __nv_bfloat16* pb, 
        ch += (int64_t)gridDim.x * WARPS) {
     const int64_t base = ch * 16;
     float lg[4], p[4];
-    forward16<false>(W, nullptr, x, n, base, use_grid ? &grid : nullptr, sd, lg);
+    forward16<false>(W, nullptr, x, nullptr, n, base, use_grid ? &grid : nullptr, sd, lg);
     softmax_pair(lg[0], lg[1], &p[0], &p[1]);
     softmax_pair(lg[2], lg[3], &p[2], &p[3]);
     const int64_t r0 = base + g, r1 = base + g + 8;
@@ -447,6 +455,18 @@ __global__ void k_adam(float* p, float* m, float* v, const float* grad, __nv_bfl
     p[i] = pi;
     pb[i] = __float2bfloat16(pi);
   }
+}
+
+// Minibatch indices for training step `step`: idx[i] uniform on [0, n) from
+// Philox4x32-10 with key = seed and counter (i, step_lo, step_hi, 4); the
+// 64-bit word w1:w0 is mapped by the high half of w * n (bias <= n / 2^64).
+__global__ void k_draw_idx(int64_t* idx, int batch, int64_t n, uint64_t seed, uint64_t step) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= batch) return;
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)step, (uint32_t)(step >> 32), 4u),
+                                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const unsigned long long u = ((unsigned long long)w.y << 32) | w.x;
+  idx[i] = (int64_t)__umul64hi(u, (unsigned long long)n);
 }
 
 __global__ void k_mlp_init(float* p, float* m, float* v, __nv_bfloat16* pb, uint64_t seed) {
@@ -620,12 +640,16 @@ int sm_count() {
 
 int status_of(cudaError_t e) { return e == cudaSuccess ? QCAMS_OK : QCAMS_E_CUDA; }
 
-bool grid_ok(const qcams_proposal_spec* s) {
+// Proposal spec check: QCAMS_E_INVALID for bad fields, QCAMS_E_CAPACITY for
+// more than 2^22 cells.
+int grid_status(const qcams_proposal_spec* s) {
   if (!s || s->n_b2 < 1 || s->n_cth < 1 || s->n_phi < 1 || s->n_eta < 1 || s->n_chi < 1)
-    return false;
+    return QCAMS_E_INVALID;
+  if (!(s->b2_max > 0) || !(s->alpha > 0) || !(s->alpha <= 1) || !(s->eps >= 0) ||
+      !std::isfinite(s->E_col))
+    return QCAMS_E_INVALID;
   const double n = (double)s->n_b2 * s->n_cth * s->n_phi * s->n_eta * s->n_chi;
-  return n <= (double)(1 << 22) && s->b2_max > 0 && s->alpha > 0 && s->alpha <= 1 &&
-         s->eps >= 0 && std::isfinite(s->E_col);
+  return n <= (double)(1 << 22) ? QCAMS_OK : QCAMS_E_CAPACITY;
 }
 
 CellGrid grid_of(const qcams_proposal_spec* s) {
@@ -640,6 +664,33 @@ CellGrid grid_of(const qcams_proposal_spec* s) {
   g.j = (float)s->j;
   g.b2_max = (float)s->b2_max;
   return g;
+}
+
+int launch_grad(const qcams_mlp* m, const float* x, const uint8_t* label, const int64_t* idx,
+                int64_t n, float* loss_out, bool zero_loss, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(m->grad, 0, NP * sizeof(float), st);
+  if (e == cudaSuccess && loss_out && zero_loss) e = cudaMemsetAsync(loss_out, 0, sizeof(float), st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  const size_t smem = sizeof(TrainSmem);
+  e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  const int64_t chunks = (n + 15) / 16;
+  int64_t grid = (chunks + WARPS * 8 - 1) / (WARPS * 8);   // ~8 chunks per warp
+  if (grid > sm_count()) grid = sm_count();
+  if (grid < 1) grid = 1;
+  k_mlp_grad<<<(unsigned)grid, THREADS, smem, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(m->params_bf16), m->params, std_of(m), x, label, idx,
+      n, m->grad, loss_out);
+  return status_of(cudaGetLastError());
+}
+
+int launch_adam(qcams_mlp* m, float lr, cudaStream_t st) {
+  m->step += 1;
+  const float c1 = (float)(1.0 - std::pow(0.9, (double)m->step));
+  const float c2 = (float)(1.0 - std::pow(0.999, (double)m->step));
+  k_adam<<<36, 256, 0, st>>>(m->params, m->adam_m, m->adam_v, m->grad,
+                             reinterpret_cast<__nv_bfloat16*>(m->params_bf16), lr, c1, c2);
+  return status_of(cudaGetLastError());
 }
 
 }  // namespace
@@ -721,22 +772,8 @@ int qcams_mlp_grad(const qcams_mlp* m, const float* x, const uint8_t* label, int
   if (!mlp_ok(m) || !x || !label || n < 1) return QCAMS_E_INVALID;
   int rc;
   if ((rc = dev_ok()) != QCAMS_OK) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   (void)cudaGetLastError();
-  cudaError_t e = cudaMemsetAsync(m->grad, 0, NP * sizeof(float), st);
-  if (e == cudaSuccess && loss_out) e = cudaMemsetAsync(loss_out, 0, sizeof(float), st);
-  if (e != cudaSuccess) return QCAMS_E_CUDA;
-  const size_t smem = sizeof(TrainSmem);
-  e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return QCAMS_E_CUDA;
-  const int64_t chunks = (n + 15) / 16;
-  int64_t grid = (chunks + WARPS * 8 - 1) / (WARPS * 8);   // ~8 chunks per warp
-  if (grid > sm_count()) grid = sm_count();
-  if (grid < 1) grid = 1;
-  k_mlp_grad<<<(unsigned)grid, THREADS, smem, st>>>(
-      reinterpret_cast<const __nv_bfloat16*>(m->params_bf16), m->params, std_of(m), x, label, n,
-      m->grad, loss_out);
-  return status_of(cudaGetLastError());
+  return launch_grad(m, x, label, nullptr, n, loss_out, true, (cudaStream_t)cuda_stream);
 }
 
 int qcams_mlp_train_step(qcams_mlp* m, const float* x, const uint8_t* label, int64_t n,
@@ -744,13 +781,30 @@ int qcams_mlp_train_step(qcams_mlp* m, const float* x, const uint8_t* label, int
   if (!(lr > 0.0f)) return QCAMS_E_INVALID;
   int rc = qcams_mlp_grad(m, x, label, n, loss_out, cuda_stream);
   if (rc != QCAMS_OK) return rc;
-  m->step += 1;
-  const float c1 = (float)(1.0 - std::pow(0.9, (double)m->step));
-  const float c2 = (float)(1.0 - std::pow(0.999, (double)m->step));
-  k_adam<<<36, 256, 0, (cudaStream_t)cuda_stream>>>(
-      m->params, m->adam_m, m->adam_v, m->grad,
-      reinterpret_cast<__nv_bfloat16*>(m->params_bf16), lr, c1, c2);
-  return status_of(cudaGetLastError());
+  return launch_adam(m, lr, (cudaStream_t)cuda_stream);
+}
+
+int qcams_mlp_train(qcams_mlp* m, const float* x, const uint8_t* label, int64_t n, int64_t steps,
+                    int32_t batch, float lr, uint64_t seed, int64_t* idx, float* losses,
+                    void* cuda_stream) {
+  if (!mlp_ok(m) || !x || !label || !idx || n < 1 || steps < 0 || batch < 1 || !(lr > 0.0f))
+    return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = dev_ok()) != QCAMS_OK) return rc;
+  (void)cudaGetLastError();
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (losses && steps > 0 &&
+      cudaMemsetAsync(losses, 0, sizeof(float) * (size_t)steps, st) != cudaSuccess)
+    return QCAMS_E_CUDA;
+  for (int64_t s = 0; s < steps; ++s) {
+    k_draw_idx<<<(batch + 255) / 256, 256, 0, st>>>(idx, batch, n, seed, (uint64_t)m->step);
+    if (cudaGetLastError() != cudaSuccess) return QCAMS_E_CUDA;
+    if ((rc = launch_grad(m, x, label, idx, batch, losses ? losses + s : nullptr, false, st)) !=
+        QCAMS_OK)
+      return rc;
+    if ((rc = launch_adam(m, lr, st)) != QCAMS_OK) return rc;
+  }
+  return QCAMS_OK;
 }
 
 int qcams_mlp_infer(const qcams_mlp* m, const float* x, int64_t n, float* probs,
@@ -772,7 +826,8 @@ int qcams_mlp_infer(const qcams_mlp* m, const float* x, int64_t n, float* probs,
 
 int qcams_build_proposal(const qcams_mlp* m, const qcams_proposal_spec* spec, double* q,
                          int64_t* qfix, int64_t* cdf, void* cuda_stream) {
-  if (!mlp_ok(m) || !grid_ok(spec) || !q || !qfix || !cdf) return QCAMS_E_INVALID;
+  if (!mlp_ok(m) || !q || !qfix || !cdf) return QCAMS_E_INVALID;
+  if (const int gs = grid_status(spec)) return gs;
   int rc;
   if ((rc = dev_ok()) != QCAMS_OK) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -794,7 +849,8 @@ int qcams_sample_proposal(const qcams_proposal_spec* spec, const int64_t* qfix,
                           const int64_t* cdf, int64_t n, uint64_t seed, uint64_t id_offset,
                           double* b, double* const* u_out, double* w, int32_t* cell,
                           void* cuda_stream) {
-  if (!grid_ok(spec) || !qfix || !cdf || n < 0 || !b || !u_out || !w || !cell) return QCAMS_E_INVALID;
+  if (!qfix || !cdf || n < 0 || !b || !u_out || !w || !cell) return QCAMS_E_INVALID;
+  if (const int gs = grid_status(spec)) return gs;
   if (!u_out[0] || !u_out[1] || !u_out[2] || !u_out[3]) return QCAMS_E_INVALID;
   if (n == 0) return QCAMS_OK;
   int rc;

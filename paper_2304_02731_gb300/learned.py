@@ -1,13 +1,14 @@
 """Learned importance-sampling proposal: orchestration of the C-ABI calls.
 
 Steps (all arithmetic in the library's kernels; this module only sequences
-calls and shuffles minibatch indices):
+calls):
 
 1. Training data: lanes of one Ca-H system drawn like the mixed study
    (E ~ U[0.05, 0.30] hartree, b^2 ~ U[0, 100] bohr^2, v in 0..10, j in
    0..20), integrated in FP64; inputs x = (E, b, v, j, theta, phi, chi, eta)
    from qcams_mlp_features, targets the outcome classes.
-2. Training: minibatch Adam steps (qcams_mlp_train_step) on shuffled data.
+2. Training: minibatch Adam steps (qcams_mlp_train: minibatch indices drawn
+   on the device, gradient over the gathered rows, Adam).
 3. Proposal at one (E, v, j): qcams_build_proposal.
 4. Estimation: lanes drawn from the proposal (qcams_sample_proposal), their
    initial states built from the drawn uniforms (qcams_init_states with
@@ -58,25 +59,17 @@ def generate(system_spec, n: int, seed: int, device="cuda", integ=None):
 
 def train(mlp: "Q.MLP", x: torch.Tensor, cls: torch.Tensor, epochs: int = 8,
           batch: int = 4096, lr: float = 2e-3, seed: int = 0, log=None):
-    """Minibatch Adam on shuffled data; returns the per-epoch mean losses."""
+    """Minibatch Adam (qcams_mlp_train: indices drawn on the device) for
+    epochs x n / batch steps; returns the per-epoch mean minibatch losses."""
     mlp.fit_standardizer(x)
-    g = torch.Generator(device=x.device)
-    g.manual_seed(seed)
     n = x.shape[0]
-    losses = []
-    for ep in range(epochs):
-        perm = torch.randperm(n, generator=g, device=x.device)
-        tot, cnt = torch.zeros((), device=x.device), 0
-        for s in range(0, n - batch + 1, batch):
-            idx = perm[s:s + batch]
-            xb, cb = x[idx].contiguous(), cls[idx].contiguous()
-            loss = mlp.train_step(xb, cb, lr)
-            tot += loss[0]
-            cnt += 1
-        losses.append(float(tot) / max(cnt, 1))
-        if log:
-            log(f"epoch {ep}: loss {losses[-1]:.4f}")
-    return losses
+    per_epoch = max(1, n // batch)
+    losses, _ = mlp.train(x, cls, epochs * per_epoch, min(batch, n), lr, seed)
+    per = losses.view(epochs, per_epoch).mean(1).cpu().numpy()
+    if log:
+        for ep, l in enumerate(per):
+            log(f"epoch {ep}: loss {l:.4f}")
+    return [float(v) for v in per]
 
 
 def best_state(host, min_count: int | None = None):

@@ -38,7 +38,7 @@ EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_i
            "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
            "qcams_debug_exp", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
            "qcams_mlp_features", "qcams_mlp_fit_standardizer", "qcams_mlp_grad",
-           "qcams_mlp_train_step", "qcams_mlp_infer", "qcams_build_proposal",
+           "qcams_mlp_train_step", "qcams_mlp_train", "qcams_mlp_infer", "qcams_build_proposal",
            "qcams_sample_proposal", "qcams_rate_constants", "qcams_gb_distribution"]
 MLP_NPARAMS = 9156
 
@@ -150,6 +150,8 @@ def lib():
                 "qcams_mlp_fit_standardizer": (C.c_int, [P(CMLP), V, I64, V]),
                 "qcams_mlp_grad": (C.c_int, [P(CMLP), V, V, I64, V, V]),
                 "qcams_mlp_train_step": (C.c_int, [P(CMLP), V, V, I64, C.c_float, V, V]),
+                "qcams_mlp_train": (C.c_int, [P(CMLP), V, V, I64, I64, I32, C.c_float,
+                                              C.c_uint64, V, V, V]),
                 "qcams_mlp_infer": (C.c_int, [P(CMLP), V, I64, V, V]),
                 "qcams_build_proposal": (C.c_int, [P(CMLP), P(ProposalSpec), V, V, V, V]),
                 "qcams_sample_proposal": (C.c_int, [P(ProposalSpec), V, V, I64, C.c_uint64,
@@ -522,6 +524,19 @@ class MLP:
                                           x.shape[0], float(lr), self.loss.data_ptr(),
                                           _stream()), "qcams_mlp_train_step")
         return self.loss
+
+    def train(self, x: torch.Tensor, cls: torch.Tensor, steps: int, batch: int, lr: float,
+              seed: int = 0):
+        """qcams_mlp_train: `steps` device-side minibatch Adam steps (indices
+        drawn with replacement).  Returns (losses [steps], last indices)."""
+        x, cls = x.contiguous(), cls.contiguous()
+        losses = torch.empty(max(int(steps), 1), dtype=torch.float32, device=x.device)
+        idx = torch.empty(int(batch), dtype=torch.int64, device=x.device)
+        _check(lib().qcams_mlp_train(C.byref(self.c), x.data_ptr(), cls.data_ptr(), x.shape[0],
+                                     int(steps), int(batch), float(lr), int(seed),
+                                     idx.data_ptr(), losses.data_ptr(), _stream()),
+               "qcams_mlp_train")
+        return losses[:int(steps)], idx
 
     def infer(self, x: torch.Tensor) -> torch.Tensor:
         x = x.contiguous()

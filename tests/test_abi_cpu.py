@@ -133,3 +133,24 @@ def test_gb_distribution_matches_oracle(Q, oracle):
     assert np.allclose(P, Po, rtol=1e-14, atol=0)
     with pytest.raises(Q.QcamsError):
         Q.gb_distribution(H, [])
+
+
+def test_proposal_spec_limits_without_a_device(Q):
+    """Proposal specs are validated before any device work: bad fields give
+    QCAMS_E_INVALID, more than 2^22 cells QCAMS_E_CAPACITY (the pointers
+    below are never dereferenced)."""
+    L = Q.lib()
+    fake = C.c_void_p(256)
+    m = Q.CMLP()
+    m.params = m.adam_m = m.adam_v = m.grad = m.params_bf16 = 256
+    big = Q.proposal_spec(0.1, 0, 0, dims=(64, 64, 32, 32, 2))      # 2^23 cells
+    assert L.qcams_build_proposal(C.byref(m), C.byref(big), fake, fake, fake, None) == -4
+    u4 = (C.c_void_p * 4)(256, 256, 256, 256)
+    assert L.qcams_sample_proposal(C.byref(big), fake, fake, 10, 0, 0, fake, u4, fake, fake,
+                                   None) == -4
+    bad = Q.proposal_spec(0.1, 0, 0, alpha=0.0)
+    assert L.qcams_build_proposal(C.byref(m), C.byref(bad), fake, fake, fake, None) == -1
+    bad = Q.proposal_spec(0.1, 0, 0, dims=(0, 8, 8, 8, 4))
+    assert L.qcams_sample_proposal(C.byref(bad), fake, fake, 10, 0, 0, fake, u4, fake, fake,
+                                   None) == -1
+    assert L.qcams_mlp_train(C.byref(m), fake, fake, 10, 1, 0, 1e-3, 0, fake, None, None) == -1

@@ -4,6 +4,8 @@ tolerances), Adam, training, the proposal table, the sampler (bit-exact
 against the oracle's sampler on the same integer proposal), and an
 end-to-end check that the importance-weighted cross section agrees with
 uniform sampling while reducing its standard error per GPU-second."""
+import math
+
 import numpy as np
 import pytest
 
@@ -121,6 +123,44 @@ def test_training_learns_a_separable_rule(Q):
     acc = np.mean(mlp.infer(xd).cpu().numpy().argmax(1) == lab)
     print(f"\nloss {first:.3f} -> {loss:.3f}, accuracy {acc:.4f}")
     assert loss < 0.3 * first and acc > 0.9
+
+
+def test_device_training_loop(Q):
+    """qcams_mlp_train: its minibatch is the rows idx drawn on the device
+    (uniform on [0, n), checked by a chi-square test), its gradient equals
+    qcams_mlp_grad on the gathered rows, and many steps learn the separable
+    rule as well as host-driven steps do."""
+    import torch
+    rng = np.random.default_rng(19)
+    n = 1000
+    x = torch.tensor(rng.normal(0, 1, (n, 8)).astype(np.float32)).cuda()
+    lab = torch.tensor(rng.integers(0, 6, n).astype(np.uint8)).cuda()
+    a, b = Q.MLP(seed=5), Q.MLP(seed=5)
+    for m in (a, b):
+        m.set_standardizer(np.zeros(8), np.ones(8))
+    losses, idx = a.train(x, lab, 1, 200_000, 1e-3, seed=8)
+    ih = idx.cpu().numpy()
+    assert ih.min() >= 0 and ih.max() < n
+    counts = np.bincount(ih, minlength=n)
+    chi2 = ((counts - 200.0) ** 2 / 200.0).sum()
+    assert chi2 < n + 5 * math.sqrt(2 * n), chi2      # dof = n - 1
+    loss_b = float(b.compute_grad(x[idx].contiguous(), lab[idx].contiguous())[0])
+    ga, gb = a.grad.cpu().numpy(), b.grad.cpu().numpy()
+    assert abs(float(losses[0]) - loss_b) <= 1e-5 * abs(loss_b)
+    assert np.allclose(ga, gb, rtol=1e-4, atol=1e-7 * np.abs(gb).max())
+    assert a.step == 1
+    # learning on device-drawn minibatches
+    m = 32768
+    xs = rng.normal(0, 1, (m, 8)).astype(np.float32)
+    ls = ((xs[:, 0] > 0).astype(int) + 2 * (xs[:, 1] > 0).astype(int)).astype(np.uint8)
+    xd, ld = torch.tensor(xs).cuda(), torch.tensor(ls).cuda()
+    net = Q.MLP(seed=3)
+    net.set_standardizer(np.zeros(8), np.ones(8))
+    lo, _ = net.train(xd, ld, 300, 2048, 3e-3, seed=1)
+    lo = lo.cpu().numpy()
+    acc = np.mean(net.infer(xd).cpu().numpy().argmax(1) == ls)
+    print(f"\ndevice loop: loss {lo[0]:.3f} -> {lo[-10:].mean():.3f}, accuracy {acc:.4f}")
+    assert lo[-10:].mean() < 0.3 * lo[0] and acc > 0.9 and net.step == 300
 
 
 def test_proposal_matches_oracle(Q, oracle):
