@@ -184,14 +184,9 @@ def oracle_rate(wl, per_cell: int, idx_offset: int = 0):
     from paper_2304_02731_gb300 import workloads as W
     import oracle as O
     O.build()
-    idx = W.stratified(wl, per_cell + idx_offset)
-    if idx_offset:
-        # skip the first idx_offset lanes of every cell (a fresh sample per step)
-        keep = []
-        starts = np.flatnonzero(np.r_[True, wl.cell[idx][1:] != wl.cell[idx][:-1]])
-        for s0, s1 in zip(starts, list(starts[1:]) + [len(idx)]):
-            keep.extend(idx[s0 + idx_offset:s1])
-        idx = np.asarray(keep)
+    # lanes idx_offset .. idx_offset + per_cell - 1 of every cell (a fresh
+    # sample per reference step)
+    idx = W.stratified(wl, per_cell, skip=idx_offset)
     cores = os.cpu_count() or 1
     ids = wl.id_offset + idx
     chunks = np.array_split(np.arange(len(idx)), cores)

@@ -80,6 +80,15 @@ __device__ __forceinline__ double pair_u(const DevPair& q, double s, const doubl
     const double x = texp(fma(-q.c0, r, q.c1), T);
     return fma(-x, x, x) * ri;
   }
+  // generic kernels (mixed systems): u = V'(r)/r with the table exponential
+  if (q.kind == QCAMS_MORSE) {
+    const double x = texp(fma(-q.c0, r, q.c1), T);
+    return q.c2 * fma(-x, x, x) * ri;
+  }
+  if (q.kind == QCAMS_BUCK) {
+    const double ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
+    return (q.c3 * ri6 * ri - q.c2 * texp(-q.c1 * r, T)) * ri;
+  }
   return pot_g(q, ri, r);
 }
 

@@ -69,7 +69,8 @@ __device__ __forceinline__ float ipowf_(float x, int n) {
   return r;
 }
 
-// u = V'(r)/r (generic) or x (1 - x)/r (Morse, factor 2 alpha De folded in kf_morse)
+// u = V'(r)/r (generic) or x (1 - x)/r (all-Morse kernels: the factor
+// 2 alpha De is folded into kf_morse)
 template <bool MORSE>
 __device__ __forceinline__ float pair_u(const PairF& q, float s) {
   const float ri = rsqrtf(s);
@@ -77,6 +78,10 @@ __device__ __forceinline__ float pair_u(const PairF& q, float s) {
   if (MORSE) {
     const float x = expf(fmaf(-q.c0, r, q.c1));
     return fmaf(-x, x, x) * ri;
+  }
+  if (q.kind == QCAMS_MORSE) {   // a Morse pair of a mixed system: V'/r = 2 alpha De x (1 - x) / r
+    const float x = expf(fmaf(-q.c0, r, q.c1));
+    return q.c2 * fmaf(-x, x, x) * ri;
   }
   const float ri2 = ri * ri;
   if (q.kind == QCAMS_LJ) return (q.c3 * ipowf_(ri, q.n) - q.c2 * ipowf_(ri, q.m)) * ri2;

@@ -136,14 +136,16 @@ def sweep_h2_ca(per_cell: int = 8192, n_E: int = 16, n_b: int = 24, b_max: float
         cell_group=group, n_groups=n_E, seed=seed)
 
 
-def stratified(w: Workload, per_cell: int) -> np.ndarray:
-    """Indices of the first `per_cell` lanes of every cell (a bounded sample
-    that spans every (E, b) cell of a sweep)."""
-    idx = []
-    starts = np.flatnonzero(np.r_[True, w.cell[1:] != w.cell[:-1]])
-    for s in starts:
-        idx.append(np.arange(s, min(s + per_cell, w.n)))
-    return np.concatenate(idx)
+def stratified(w: Workload, per_cell: int, skip: int = 0) -> np.ndarray:
+    """Sorted indices of lanes skip .. skip + per_cell - 1 (in lane order) of
+    every cell: a bounded sample that spans every cell, whether or not the
+    lanes of a cell are contiguous."""
+    order = np.argsort(w.cell, kind="stable")
+    c = w.cell[order]
+    starts = np.flatnonzero(np.r_[True, c[1:] != c[:-1]])
+    ends = np.r_[starts[1:], len(c)]
+    idx = [order[min(s + skip, e):min(s + skip + per_cell, e)] for s, e in zip(starts, ends)]
+    return np.sort(np.concatenate(idx)) if idx else np.zeros(0, np.int64)
 
 
 def mixed_ca_h(n: int = 2_000_000, seed: int = 0, n_E_bins: int = 10) -> Workload:
