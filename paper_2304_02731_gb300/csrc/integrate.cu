@@ -120,20 +120,21 @@ __device__ __forceinline__ void accel(const DevSys& S, const double* __restrict_
 }
 
 // Position of stage s (1-based, s >= 2).
+// The stage's coefficients h^2 (A^2)_{sq} are formed once per stage (s - 2
+// multiplies) rather than scaling each component's sum by h^2 (6 multiplies).
 template <int s>
 __device__ __forceinline__ void stage_x(const double* rho, const double* vel, const double (*acc)[6],
                                         double h, double hh, double* x) {
   const double hc = h * kT.c[s];
+  double w[s > 2 ? s - 2 : 1];
+#pragma unroll
+  for (int q = 1; q <= s - 2; ++q) w[q - 1] = hh * kT.a2[s][q];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    if (s == 2) {
-      x[i] = fma(hc, vel[i], rho[i]);   // (A^2)_{2q} = 0: no acceleration term
-    } else {
-      double sum = kT.a2[s][1] * acc[0][i];
+    double xi = fma(hc, vel[i], rho[i]);   // (A^2)_{2q} = 0: stage 2 has no acceleration term
 #pragma unroll
-      for (int q = 2; q <= s - 2; ++q) sum = fma(kT.a2[s][q], acc[q - 1][i], sum);
-      x[i] = fma(hh, sum, fma(hc, vel[i], rho[i]));
-    }
+    for (int q = 1; q <= s - 2; ++q) xi = fma(w[q - 1], acc[q - 1][i], xi);
+    x[i] = xi;
   }
 }
 

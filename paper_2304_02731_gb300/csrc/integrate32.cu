@@ -144,11 +144,14 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
 #define QCAMS_STAGE(sIdx)                                                            \
   {                                                                                  \
     const float hc = h * kTf.c[sIdx];                                                \
+    float w[(sIdx) - 2];                                                             \
+    _Pragma("unroll") for (int q = 1; q <= (sIdx) - 2; ++q)                          \
+        w[q - 1] = hh * kTf.a2[sIdx][q];                                             \
     _Pragma("unroll") for (int i = 0; i < 6; ++i) {                                  \
-      float sum = kTf.a2[sIdx][1] * L.acc[0][i];                                     \
-      _Pragma("unroll") for (int q = 2; q <= (sIdx) - 2; ++q)                        \
-          sum = fmaf(kTf.a2[sIdx][q], L.acc[q - 1][i], sum);                         \
-      x[i] = fmaf(hh, sum, fmaf(hc, L.vel[i], L.rho[i]));                            \
+      float xi = fmaf(hc, L.vel[i], L.rho[i]);                                       \
+      _Pragma("unroll") for (int q = 1; q <= (sIdx) - 2; ++q)                        \
+          xi = fmaf(w[q - 1], L.acc[q - 1][i], xi);                                  \
+      x[i] = xi;                                                                     \
     }                                                                                \
     accel<MORSE>(S, x, L.acc[(sIdx) - 1], s2);                                       \
   }

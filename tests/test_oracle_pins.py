@@ -656,4 +656,3 @@ def test_gb_distribution_normalisation_and_integer_case(oracle):
         for v in range(12):
             ncv = np.sum(sel & (cls == c) & (vt == v))
             assert P[c, v] == pytest.approx(ncv / (nb + Nd / peak), rel=1e-9, abs=1e-15)
-
