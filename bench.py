@@ -34,17 +34,17 @@ if ROOT not in sys.path:
 # FP64 floating-point operations per attempted integrator step of the Morse
 # kernel: 2 dfma + dmul + dadd, from ncu sass counters on the profile case
 # (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 540 DFMA,
-# 230 DMUL, 19 DADD per lane-step, six right-hand sides included.  The FP64
-# pipe issues 540 + 230 + 19 = 789 instructions per step; the DFMA-chain
+# 215 DMUL, 19 DADD per lane-step, six right-hand sides included.  The FP64
+# pipe issues 540 + 215 + 19 = 774 instructions per step; the DFMA-chain
 # peak runs one DFMA (2 FLOP) per pipe slot, so pipe_frac below is the
 # fraction of the pipe's instruction rate the kernel uses.
-FP64_FLOP_PER_STEP = 1329
-FP64_INSTR_PER_STEP = 789
+FP64_FLOP_PER_STEP = 1314
+FP64_INSTR_PER_STEP = 774
 # FP32 floating-point operations per attempted step of the FP32 Morse kernel
 # (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
-# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 506 FFMA,
-# 216 FMUL, 57 FADD per lane-step); it also issues one DADD (the time).
-FP32_FLOP_PER_STEP = 1286
+# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 476 FFMA,
+# 226 FMUL, 57 FADD per lane-step); it also issues one DADD (the time).
+FP32_FLOP_PER_STEP = 1236
 # DRAM bytes per trajectory of the integrator (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum on the profile case, 686,080 B for 3,840 lanes; the
 # state is loaded once and stored once, everything else is in registers).

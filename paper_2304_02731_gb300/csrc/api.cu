@@ -26,10 +26,10 @@ constexpr int kMaxLevelsReq = 65536;
 constexpr int kMaxCells = 65536;
 
 // Gauss-Legendre rules in the sine-mapped variable (positive half of the
-// symmetric nodes, written by gen_gl_tables.py): 64 points for the per-lane
+// symmetric nodes, written by gen_gl_tables.py): 48 points for the per-lane
 // action integral, 128 for the level solver.  Compile-time constants, so
 // every entry point can use them without a context.
-constexpr int kGL64 = 64, kGL128 = 128;
+constexpr int kGL48 = 48, kGL128 = 128;
 #include "gl_tables.inc"
 
 std::mutex g_mutex;
@@ -310,10 +310,13 @@ __device__ __forceinline__ double pot_dV_(const DevPair& q, double r, const doub
   const double ri = 1.0 / r, ri2 = ri * ri;
   return q.c3 * ri2 * ri2 * ri2 * ri - q.c2 * texp(-q.c1 * r, T);
 }
+// V_eff = V + L2/(2 mu r^2); the centrifugal term from 1/r^2 = rsqrt(r^2)^2
+// (no division in the root-search loops).
 template <bool TAB>
 __device__ __forceinline__ double veff_(const DevPair& q, double mu, double L2, double r,
                                         const double* T) {
-  return pot_V_<TAB>(q, r, T) + L2 / (2.0 * mu * r * r);
+  const double ri = rsqrt(r * r);
+  return pot_V_<TAB>(q, r, T) + (0.5 * L2 / mu) * (ri * ri);
 }
 template <bool TAB>
 __device__ __forceinline__ double gfun_(const DevPair& q, double r, const double* T) {
@@ -424,16 +427,17 @@ __device__ void action_period(const DevPair& q, double mu, double L2, double E, 
   double sa = 0.0, sp = 0.0;
 #pragma unroll 4
   for (int k = 0; k < NG / 2; ++k) {
-    const double sn = (NG == kGL64) ? kGL64S[k] : kGL128S[k];
-    const double wc = (NG == kGL64) ? kGL64WC[k] : kGL128WC[k];
+    const double sn = (NG == kGL48) ? kGL48S[k] : kGL128S[k];
+    const double wc = (NG == kGL48) ? kGL48WC[k] : kGL128WC[k];
 #pragma unroll
     for (int sgn = 0; sgn < 2; ++sgn) {
       const double r = sgn ? fma(-d, sn, c) : fma(d, sn, c);
-      const double g = E - (pot_V_<TAB>(q, r, T) + a / (r * r));
+      const double ri = rsqrt(r * r);   // 1/r and sqrt(g) from reciprocal square roots
+      const double g = E - (pot_V_<TAB>(q, r, T) + a * ri * ri);
       if (g > 0.0) {
-        const double sq = sqrt(g);
-        sa = fma(wc, sq, sa);
-        if (PERIOD) sp += wc / sq;
+        const double rg = rsqrt(g);
+        sa = fma(wc, g * rg, sa);
+        if (PERIOD) sp = fma(wc, rg, sp);
       }
     }
   }
@@ -716,7 +720,7 @@ __global__ void __launch_bounds__(128) k_analyze(SysSet sys, const DevShape* sha
         double rm, rp, act, per;
         vp = -0.5;
         if (turning_points<true>(q, sh, mu, L2, E, r_in, r_top, sT, &rm, &rp)) {
-          action_period<kGL64, true, false>(q, mu, L2, E, rm, rp, sT, &act, &per);
+          action_period<kGL48, true, false>(q, mu, L2, E, rm, rp, sT, &act, &per);
           vp = -0.5 + sqrt(2.0 * mu) / kPi * act;
         }
         jp = -0.5 + 0.5 * sqrt(1.0 + 4.0 * L2);
