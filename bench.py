@@ -42,13 +42,19 @@ FP64_FLOP_PER_STEP = 1314
 FP64_INSTR_PER_STEP = 774
 # FP32 floating-point operations per attempted step of the FP32 Morse kernel
 # (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
-# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 476 FFMA,
-# 226 FMUL, 57 FADD per lane-step); it also issues one DADD (the time).
-FP32_FLOP_PER_STEP = 1236
-# DRAM bytes per trajectory of the integrator (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum on the profile case, 686,080 B for 3,840 lanes; the
-# state is loaded once and stored once, everything else is in registers).
-DRAM_BYTES_PER_LANE = 686080 / 3840
+# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 404 FFMA,
+# 226 FMUL, 39 FADD per lane-step); it also issues one DADD (the time).  The
+# kernel is bound by instruction issue: 1,000 thread instructions per step
+# (all pipes), so issue_frac below is the fraction of the SMs' issue rate
+# (4 warp instructions per SM per cycle) it uses.
+FP32_FLOP_PER_STEP = 1074
+FP32_THREAD_INSTR_PER_STEP = 1000
+# DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of the FP64 profile case (1,197,312 B for 3,840
+# lanes in 30 blocks) less the 30 blocks' 16 KB exponential tables (a fixed
+# cost per resident block, ~5 MB for a full-size launch), per lane: the state
+# is loaded once and stored once, everything else is in registers.
+DRAM_BYTES_PER_LANE = (1197312 - 30 * 16384) / 3840
 
 
 def parse():
@@ -378,7 +384,7 @@ def run_ours(args):
                 "peak_source": f"measured FP{args.precision} FMA-chain microbenchmark "
                                f"(qcams_fma_peak), this run",
                 "traffic": DRAM_BYTES_PER_LANE * wl.n if args.workload == "sweep" else None,
-                "traffic_note": "ncu dram bytes of the 3,840-lane profile case scaled by lanes"}
+                "traffic_note": "ncu dram bytes of the 3,840-lane profile case (less its per-block exp tables) scaled by lanes"}
     if args.workload in ("sweep", "plain"):
         # FLOP counts are those of the Morse kernel (H2 + Ca systems)
         ach = flop_per_step * steps_per_launch / (avg_integ_ms * 1e-3)
@@ -386,6 +392,13 @@ def run_ours(args):
         if args.precision == 64:
             rate = FP64_INSTR_PER_STEP * steps_per_launch / (avg_integ_ms * 1e-3)
             roofline.update(fp64_instr_per_step=FP64_INSTR_PER_STEP, pipe_frac=rate / (peak / 2))
+        else:
+            props = torch.cuda.get_device_properties(dev)
+            mhz = (clock_info or {}).get("sm_mhz") or 2070.0
+            issue = props.multi_processor_count * 4 * 32 * mhz * 1e6   # thread instructions / s
+            rate = FP32_THREAD_INSTR_PER_STEP * steps_per_launch / (avg_integ_ms * 1e-3)
+            roofline.update(thread_instr_per_step=FP32_THREAD_INSTR_PER_STEP,
+                            issue_frac=rate / issue)
     else:
         roofline.update(achieved=None, frac=None)
     roofline.update(steps_per_launch=steps_per_launch, integrate_ms=avg_integ_ms,
