@@ -6,6 +6,7 @@ _build/ directory (git-ignored)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -36,7 +37,19 @@ def _deps():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Build (or reuse) the library.  Processes that build at the same time
+    (one per rank under torchrun) take turns through a lock file, so no
+    object file is rewritten while another process links it."""
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
     nvcc = _nvcc()
