@@ -1,7 +1,7 @@
 // Oracle of the learned importance-sampling proposal (test infrastructure
 // only; see qcams_oracle.cpp for the rules that apply to the whole oracle).
 //
-// The network is the one the QCT outcome study specifies: 8 inputs (E_col,
+// The network of the learned-proposal extension (not part of the paper): 8 inputs (E_col,
 // b, v, j, theta, phi, chi, eta), three hidden layers of width 64 with the
 // SiLU activation z sigmoid(z), 4 outcome logits (Q, R_AC, R_BC, D), softmax
 // cross-entropy loss, Adam (Kingma & Ba, "Adam: a method for stochastic

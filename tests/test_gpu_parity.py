@@ -244,18 +244,21 @@ def test_empty_and_invalid_lanes(Q):
     b0 = Q.Batch.empty(0, "cuda")
     Q.init_states([W.SYS_H2_CA_MORSE], b0, [], [], [], [], 30.0, 0)
     Q.run_batch([W.SYS_H2_CA_MORSE], b0, Q.make_integ())
-    n = 5
-    batch = Q.Batch.empty(n, "cuda", sys_id=[0, 0, 0, 3, 0])
-    E = [0.1, -0.1, 0.1, 0.1, 0.1]
-    b = [1.0, 1.0, 50.0, 1.0, 1.0]
-    v = [0, 0, 0, 0, 70]
-    j = [0, 0, 0, 0, 0]
+    n = 8
+    batch = Q.Batch.empty(n, "cuda", sys_id=[0, 0, 0, 3, 0, 0, 0, -1])
+    E = [0.1, -0.1, 0.1, 0.1, 0.1, float("nan"), 0.1, 0.1]
+    b = [1.0, 1.0, 50.0, 1.0, 1.0, 1.0, float("nan"), 1.0]
+    v = [0, 0, 0, 0, 70, 0, 0, 0]
+    j = [0, 0, 0, 0, 0, 0, 0, 0]
     Q.init_states([W.SYS_H2_CA_MORSE], batch, E, b, v, j, 30.0, 0)
     Q.run_batch([W.SYS_H2_CA_MORSE], batch, Q.make_integ())
     torch.cuda.synchronize()
     st = batch.status.cpu().numpy()
-    assert list(st) == [2, 9, 9, 9, 8]
-    assert list(batch.cls.cpu().numpy()) == [0, 5, 5, 5, 5]
+    # valid; E <= 0; R <= b; system out of range; v beyond the table; NaN E;
+    # NaN b; negative system index
+    assert list(st) == [2, 9, 9, 9, 8, 9, 9, 9]
+    assert list(batch.cls.cpu().numpy()) == [0, 5, 5, 5, 5, 5, 5, 5]
+    assert np.all(np.isfinite(batch.y.cpu().numpy()))
 
 
 HEAVY_MORSE = dict(mass_u=(126.904, 126.904, 40.078),
