@@ -468,7 +468,7 @@ def run_learned(args):
     t_gen = time.perf_counter() - t0
     mlp = Q.MLP(seed=1)
     t0 = time.perf_counter()
-    losses = L.train(mlp, x, cls, epochs=8, batch=8192, lr=2e-3)
+    losses = L.train(mlp, x, cls, epochs=24, batch=8192, lr=2e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     v, j, frac = L.best_state(host)

@@ -557,7 +557,7 @@ class MLP:
 
 
 def proposal_spec(E_col, v, j, dims=(16, 8, 8, 8, 4), b2_max=100.0, eps=1e-3,
-                  alpha=0.2) -> ProposalSpec:
+                  alpha=0.1) -> ProposalSpec:
     s = ProposalSpec()
     s.E_col, s.v, s.j = float(E_col), int(v), int(j)
     s.n_b2, s.n_cth, s.n_phi, s.n_eta, s.n_chi = (int(d) for d in dims)
