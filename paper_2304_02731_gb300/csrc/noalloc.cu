@@ -88,8 +88,6 @@ extern "C" int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys,
                          integ->blocks_per_sm, scratch_ctx, st);
   if (e != cudaSuccess) return QCAMS_E_CUDA;
   if (integ->fixed_step) return QCAMS_OK;
-  const double sg =
-      integ->gb_sigma > 0 ? integ->gb_sigma : 0.1 / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-  e = launch_analyze(ss, shapes, sg, d, st);
+  e = launch_analyze(ss, shapes, ip.gb_sigma, d, st);
   return e == cudaSuccess ? QCAMS_OK : QCAMS_E_CUDA;
 }

@@ -29,6 +29,7 @@ struct Ctx {
 
 struct IntegParams {
   double rtol, atol, r_stop2, t_stop, h_fixed;
+  double gb_sigma;       // Gaussian-binning width of the product analysis
   long long max_steps;
   int fixed_step;
   float rtol_f, atol_f;  // error-norm constants in FP32
