@@ -113,18 +113,19 @@ def _oracle_chunk(payload):
     specs, sid, E, b, v, j, R0, seed, ids, integ_kw = payload
     systems = [O.system_from_spec(sp) for sp in specs]
     integ = O.make_integ(**integ_kw)
-    cls = np.zeros(len(E), np.int32)
+    out = np.zeros((len(E), 4), np.int32)    # cls, v_t, j_t, status
     for k in range(len(E)):
         _, res = O.run_lanes(systems, sid[k:k + 1], E[k:k + 1], b[k:k + 1], v[k:k + 1],
                              j[k:k + 1], R0, seed, integ, id_offset=int(ids[k]))
-        cls[k] = res["cls"][0]
-    return cls
+        out[k] = (res["cls"][0], res["vt"][0], res["jt"][0], res["status"][0])
+    return out
 
 
 @pytest.fixture(scope="module")
 def oracle_sample(full_run, oracle):
-    """The oracle's classes for 16 lanes per (E, b) cell of the sweep (6,144
-    trajectories run one by one, one oracle process per host core)."""
+    """The oracle's outcomes (class, v_t, j_t, status) for 16 lanes per
+    (E, b) cell of the sweep (6,144 trajectories run one by one, one oracle
+    process per host core)."""
     import multiprocessing as mp
     import os
     wl = full_run[0]
@@ -134,11 +135,12 @@ def oracle_sample(full_run, oracle):
     payloads = [(wl.systems, wl.sys_id[idx[c]], wl.E[idx[c]], wl.b[idx[c]], wl.v[idx[c]],
                  wl.j[idx[c]], wl.R0, wl.seed, idx[c], dict(wl.integ)) for c in parts]
     with mp.get_context("spawn").Pool(len(payloads)) as pool:
-        cls_o = np.concatenate(pool.map(_oracle_chunk, payloads))
-    return idx, cls_o
+        res = np.concatenate(pool.map(_oracle_chunk, payloads))
+    return idx, res
 
 
-def _within_3se(wl, groups, idx, cls_o, oracle):
+def _within_3se(wl, groups, idx, res, oracle):
+    cls_o = res[:, 0]
     zeros = np.zeros(len(idx), np.int32)
     h_o = oracle.reduce(cls_o, zeros, zeros, np.zeros(len(idx)), wl.cell[idx], wl.n_cells)
     _, g_o = oracle.xsec(h_o, wl.cell_b, wl.cell_w, wl.cell_group, wl.n_groups)
@@ -165,6 +167,46 @@ def test_full_size_cross_sections_within_3se_of_oracle(full_run, oracle_sample, 
     wl, out, hist, cells, groups = full_run
     worst = _within_3se(wl, groups, *oracle_sample, oracle)
     print(f"\nlargest |sigma_gpu - sigma_oracle| / SE over 16 energies x 4 channels: {worst:.2f}")
+
+
+def test_full_size_product_states_match_oracle(full_run, oracle_sample):
+    """Product analysis at full size (v' from the action integral, j' from
+    L^2).  Lane by lane on the 6,144 oracle lanes: where both sides reached
+    the same product by r_stop, the integer bins (v_t, j_t) agree for
+    >= 97 % (a bin flips only when v' or j' sits within the two
+    trajectories' rounding-level difference of a half-integer, or when a
+    long complex ends differently).  As distributions: in each quarter of
+    the energy range, the oracle sample's quench v_t and j_t histograms are
+    consistent (chi-square, p > 1e-4) with the full GPU sweep's."""
+    from scipy import stats
+    wl, out, hist, cells, groups = full_run
+    idx, res = oracle_sample
+    cls_o, vt_o, jt_o, st_o = res.T
+    same = (out["status"][idx] == 2) & (st_o == 2) & (out["cls"][idx] == cls_o) & (cls_o <= 2)
+    agree = np.mean((out["vt"][idx][same] == vt_o[same]) & (out["jt"][idx][same] == jt_o[same]))
+    print(f"\n(v_t, j_t) agreement on {same.sum()} product lanes: {agree:.4f}")
+    assert same.sum() > 4500 and agree >= 0.97
+    e_idx = wl.cell // 24                       # energy index of each lane (24 b per energy)
+    worst = 1.0
+    for band in range(4):
+        g_sel = (e_idx // 4 == band) & (out["cls"] == 0) & (out["status"] == 2)
+        o_sel = (e_idx[idx] // 4 == band) & (cls_o == 0) & (st_o == 2)
+        for gv, ov in ((out["vt"][g_sel], vt_o[o_sel]), (out["jt"][g_sel], jt_o[o_sel])):
+            top = int(max(gv.max(), ov.max())) + 1
+            pg = np.bincount(gv, minlength=top) / len(gv)
+            co = np.bincount(ov, minlength=top).astype(float)
+            exp = pg * len(ov)
+            keep = exp >= 5                     # pool the sparse bins into one
+            obs_b = np.r_[co[keep], co[~keep].sum()]
+            exp_b = np.r_[exp[keep], exp[~keep].sum()]
+            if exp_b[-1] < 5:
+                obs_b, exp_b = obs_b[:-1], exp_b[:-1]
+                exp_b *= obs_b.sum() / exp_b.sum()
+            chi2 = np.sum((obs_b - exp_b) ** 2 / exp_b)
+            p = stats.chi2.sf(chi2, len(obs_b) - 1)
+            worst = min(worst, p)
+            assert p > 1e-4, (band, chi2, len(obs_b))
+    print(f"smallest chi-square p-value over 4 energy bands x (v_t, j_t): {worst:.3g}")
 
 
 def test_fp32_full_size_against_fp64_oracle(full_run, oracle_sample, oracle):
