@@ -113,17 +113,18 @@ def _oracle_chunk(payload):
     specs, sid, E, b, v, j, R0, seed, ids, integ_kw = payload
     systems = [O.system_from_spec(sp) for sp in specs]
     integ = O.make_integ(**integ_kw)
-    out = np.zeros((len(E), 4), np.int32)    # cls, v_t, j_t, status
+    out = np.zeros((len(E), 5), np.int32)    # cls, v_t, j_t, status, accepted steps
     for k in range(len(E)):
         _, res = O.run_lanes(systems, sid[k:k + 1], E[k:k + 1], b[k:k + 1], v[k:k + 1],
                              j[k:k + 1], R0, seed, integ, id_offset=int(ids[k]))
-        out[k] = (res["cls"][0], res["vt"][0], res["jt"][0], res["status"][0])
+        out[k] = (res["cls"][0], res["vt"][0], res["jt"][0], res["status"][0],
+                  res["nsteps"][0])
     return out
 
 
 @pytest.fixture(scope="module")
 def oracle_sample(full_run, oracle):
-    """The oracle's outcomes (class, v_t, j_t, status) for 16 lanes per
+    """The oracle's outcomes (class, v_t, j_t, status, steps) for 16 lanes per
     (E, b) cell of the sweep (6,144 trajectories run one by one, one oracle
     process per host core)."""
     import multiprocessing as mp
@@ -171,21 +172,28 @@ def test_full_size_cross_sections_within_3se_of_oracle(full_run, oracle_sample, 
 
 def test_full_size_product_states_match_oracle(full_run, oracle_sample):
     """Product analysis at full size (v' from the action integral, j' from
-    L^2).  Lane by lane on the 6,144 oracle lanes: where both sides reached
-    the same product by r_stop, the integer bins (v_t, j_t) agree for
-    >= 97 % (a bin flips only when v' or j' sits within the two
-    trajectories' rounding-level difference of a half-integer, or when a
-    long complex ends differently).  As distributions: in each quarter of
-    the energy range, the oracle sample's quench v_t and j_t histograms are
-    consistent (chi-square, p > 1e-4) with the full GPU sweep's."""
+    L^2).  Lane by lane on the 6,144 oracle lanes that reached the same
+    product by r_stop on both sides: where the two trajectories stayed
+    together (accepted step counts within 2 %), the integer bins (v_t, j_t)
+    agree for >= 99.5 % (a bin flips only when v' or j' lies within the
+    rounding-level difference of a half-integer); over all of them, which
+    include chaotic complexes that separate long before the end, for
+    >= 95 %.  As distributions: in each quarter of the energy range, the
+    oracle sample's quench v_t and j_t histograms are consistent
+    (chi-square, p > 1e-4) with the full GPU sweep's."""
     from scipy import stats
     wl, out, hist, cells, groups = full_run
     idx, res = oracle_sample
-    cls_o, vt_o, jt_o, st_o = res.T
+    cls_o, vt_o, jt_o, st_o, ns_o = res.T
     same = (out["status"][idx] == 2) & (st_o == 2) & (out["cls"][idx] == cls_o) & (cls_o <= 2)
-    agree = np.mean((out["vt"][idx][same] == vt_o[same]) & (out["jt"][idx][same] == jt_o[same]))
-    print(f"\n(v_t, j_t) agreement on {same.sum()} product lanes: {agree:.4f}")
-    assert same.sum() > 4500 and agree >= 0.97
+    bins = (out["vt"][idx] == vt_o) & (out["jt"][idx] == jt_o)
+    ns_g = out["nsteps"][idx].astype(float)
+    close = same & (np.abs(ns_g - ns_o) <= 0.02 * ns_o)
+    agree_all, agree_close = np.mean(bins[same]), np.mean(bins[close])
+    print(f"\n(v_t, j_t) agreement: {agree_close:.4f} on {close.sum()} lanes whose trajectories "
+          f"stayed together, {agree_all:.4f} on all {same.sum()} product lanes")
+    assert same.sum() > 4500 and close.sum() > 0.8 * same.sum()
+    assert agree_close >= 0.995 and agree_all >= 0.95
     e_idx = wl.cell // 24                       # energy index of each lane (24 b per energy)
     worst = 1.0
     for band in range(4):
