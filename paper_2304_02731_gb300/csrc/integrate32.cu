@@ -45,6 +45,15 @@ __constant__ RknTabF kTf = make_rkn_tab_f();
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// Approximate reciprocal (one MUFU instruction, about 1 ulp): the error norm
+// needs only a few significant bits, and the scales it divides by are
+// positive and far from the FP32 range limits (atol > 0).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // FP32 copies of the per-system constants (built on the host, so the kernel
 // never converts doubles in its inner loop).
 struct PairF {
@@ -205,9 +214,9 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
     yv[i] = dv[i] - L.cvel[i];
     vn[i] = L.vel[i] + yv[i];
     const float scr = fmaf(ip.rtol_f, fmaxf(fabsf(L.rho[i]), fabsf(x[i])), ip.atol_f);
-    const float qr = __fdividef(er[i], scr);
+    const float qr = er[i] * rcp_approx(scr);
     const float scv = fmaf(ip.rtol_f, fmaxf(fabsf(L.vel[i]), fabsf(vn[i])), L.atv[i / 3]);
-    const float qv = __fdividef(ev[i], scv);
+    const float qv = ev[i] * rcp_approx(scv);
     sum = fmaf(qr, qr, fmaf(qv, qv, sum));
   }
   const float en2 = sum * (1.0f / 12.0f);

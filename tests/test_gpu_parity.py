@@ -150,6 +150,21 @@ def test_adaptive_plain_study_parity(Q, oracle):
     assert np.median(steps_rel) < 0.01
     rel = np.abs(g["dE"]) / np.maximum(np.abs(g["E0"]), wl.E)
     assert np.all(rel[g["status"] == 2] < 1e-8)
+    # total angular momentum rho1 x P1 + rho2 x P2 (an invariant that RK
+    # keeps only to its tolerance): the GPU conserves it as well as the
+    # oracle does, lane by lane (initial states: the oracle's, equal to the
+    # GPU's to 1e-11)
+    y0 = oracle.init(_osys(oracle, wl.systems), wl.sys_id, wl.E, wl.b, wl.v, wl.j, wl.R0,
+                     wl.seed, wl.id_offset)["y"]
+
+    def drift(y1):
+        L0 = np.cross(y0[:, 0:3], y0[:, 6:9]) + np.cross(y0[:, 3:6], y0[:, 9:12])
+        L1 = np.cross(y1[:, 0:3], y1[:, 6:9]) + np.cross(y1[:, 3:6], y1[:, 9:12])
+        return np.linalg.norm(L1 - L0, axis=1) / np.maximum(np.linalg.norm(L0, axis=1), 1.0)
+    dL, dL_o = drift(g["y"]), drift(st["y"])
+    print(f"max |dL|/max(|L|, 1): GPU {dL.max():.2e}, oracle {dL_o.max():.2e}; "
+          f"median GPU {np.median(dL):.2e}, oracle {np.median(dL_o):.2e}")
+    assert np.all(dL <= np.maximum(1e-8, 3.0 * dL_o))
     # integer histograms from the GPU's per-lane outcomes: bit-exact
     ho = oracle.reduce(g["cls"], g["vt"], g["jt"], g["gbw"], wl.cell, wl.n_cells)
     assert np.array_equal(hist.cpu().numpy(), ho)
