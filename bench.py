@@ -44,17 +44,20 @@ FP64_INSTR_PER_STEP = 774
 # (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
 # profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 404 FFMA,
 # 226 FMUL, 39 FADD per lane-step); it also issues one DADD (the time).  The
-# kernel is bound by instruction issue: 1,000 thread instructions per step
+# kernel is bound by instruction issue: 963 thread instructions per step
 # (all pipes), so issue_frac below is the fraction of the SMs' issue rate
 # (4 warp instructions per SM per cycle) it uses.
 FP32_FLOP_PER_STEP = 1074
-FP32_THREAD_INSTR_PER_STEP = 1000
+FP32_THREAD_INSTR_PER_STEP = 963
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of the FP64 profile case (1,197,312 B for 3,840
 # lanes in 30 blocks) less the 30 blocks' 16 KB exponential tables (a fixed
 # cost per resident block, ~5 MB for a full-size launch), per lane: the state
 # is loaded once and stored once, everything else is in registers.
 DRAM_BYTES_PER_LANE = (1197312 - 30 * 16384) / 3840
+# The same for the FP32 kernel (561,152 B read, no table): its state is
+# loaded as (value, compensation) pairs from the same FP64 arrays.
+DRAM_BYTES_PER_LANE_FP32 = 561152 / 3840
 
 
 def parse():
@@ -383,7 +386,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "unit": "TFLOP/s", "peak": peak / 1e12,
                 "peak_source": f"measured FP{args.precision} FMA-chain microbenchmark "
                                f"(qcams_fma_peak), this run",
-                "traffic": DRAM_BYTES_PER_LANE * wl.n if args.workload == "sweep" else None,
+                "traffic": ((DRAM_BYTES_PER_LANE if args.precision == 64 else DRAM_BYTES_PER_LANE_FP32)
+                            * wl.n if args.workload == "sweep" else None),
                 "traffic_note": "ncu dram bytes of the 3,840-lane profile case (less its per-block exp tables) scaled by lanes"}
     if args.workload in ("sweep", "plain"):
         # FLOP counts are those of the Morse kernel (H2 + Ca systems)
