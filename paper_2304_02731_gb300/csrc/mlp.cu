@@ -675,7 +675,11 @@ int launch_grad(const qcams_mlp* m, const float* x, const uint8_t* label, const 
   e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return QCAMS_E_CUDA;
   const int64_t chunks = (n + 15) / 16;
-  int64_t grid = (chunks + WARPS * 8 - 1) / (WARPS * 8);   // ~8 chunks per warp
+  // ~2 chunks of 16 samples per warp, at most one block per SM (the block
+  // holds the weights and its gradient in 160 KB of shared memory): a batch
+  // of 8,192 samples spreads over 64 SMs, and each block's one flush of its
+  // gradient (9,156 global atomics) is amortised over 128 samples
+  int64_t grid = (chunks + WARPS * 2 - 1) / (WARPS * 2);
   if (grid > sm_count()) grid = sm_count();
   if (grid < 1) grid = 1;
   k_mlp_grad<<<(unsigned)grid, THREADS, smem, st>>>(
