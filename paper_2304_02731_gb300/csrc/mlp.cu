@@ -61,9 +61,26 @@ struct WarpSmem {
   __nv_bfloat16 at[3][H][16 + PK];  // A1^T, A2^T, A3^T [unit][sample]
   __nv_bfloat16 dzt[H][16 + PK];    // dZ^T [unit][sample]
 };
+// The block's gradient accumulator in shared memory: the parameter layout
+// with the rows of W2, W3 and W4 padded from 64 to 68 floats, so that the
+// eight rows an MMA fragment adds into fall on different banks (2-way
+// instead of 8-way conflicts of the shared atomics).
+constexpr int GLD = 68;
+constexpr int SW1 = 0, SB1 = SW1 + H * IN, SW2 = SB1 + H, SB2 = SW2 + H * GLD, SW3 = SB2 + H,
+              SB3 = SW3 + H * GLD, SW4 = SB3 + H, SB4 = SW4 + OUT * GLD, NPS = SB4 + OUT;
+// Position in the padded accumulator of parameter i (linear layout).
+__device__ __forceinline__ int padded(int i) {
+  if (i >= OW2 && i < OB2) return SW2 + ((i - OW2) >> 6) * GLD + ((i - OW2) & 63);
+  if (i >= OW3 && i < OB3) return SW3 + ((i - OW3) >> 6) * GLD + ((i - OW3) & 63);
+  if (i >= OW4 && i < OB4) return SW4 + ((i - OW4) >> 6) * GLD + ((i - OW4) & 63);
+  if (i < OW2) return i;                     // W1, b1 (no padding before them)
+  if (i < OW3) return i - OB2 + SB2;         // b2
+  if (i < OW4) return i - OB3 + SB3;         // b3
+  return i - OB4 + SB4;                      // b4
+}
 struct TrainSmem {
   WeightsSmem w;
-  float grad[NP];
+  float grad[NPS];
   WarpSmem warp[WARPS];
 };
 
@@ -250,9 +267,9 @@ __device__ __forceinline__ void softmax_pair(float z0, float z1, float* p0, floa
 }
 
 // dW (+)= dZ^T A for one layer: M = n_out (16-row tiles), K = 16 samples,
-// N = n_in (8-column tiles), into the CTA gradient accumulator.
+// N = n_in (8-column tiles), into the CTA gradient accumulator (row stride ld).
 __device__ void accumulate_dw(const WarpSmem* ws, const __nv_bfloat16 (*aT)[16 + PK], int m_tiles,
-                              int n_tiles, int n_out_valid, int n_in, float* gW) {
+                              int n_tiles, int n_out_valid, int n_in, int ld, float* gW) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   for (int mt = 0; mt < m_tiles; ++mt) {
     uint32_t a[4];
@@ -265,12 +282,12 @@ __device__ void accumulate_dw(const WarpSmem* ws, const __nv_bfloat16 (*aT)[16 +
       mma(d, a, ld2(&aT[8 * nt + g][2 * q]), ld2(&aT[8 * nt + g][8 + 2 * q]));
       const int r0 = 16 * mt + g, r1 = r0 + 8, col = 8 * nt + 2 * q;
       if (r0 < n_out_valid && col < n_in) {
-        atomicAdd(&gW[r0 * n_in + col], d[0]);
-        atomicAdd(&gW[r0 * n_in + col + 1], d[1]);
+        atomicAdd(&gW[r0 * ld + col], d[0]);
+        atomicAdd(&gW[r0 * ld + col + 1], d[1]);
       }
       if (r1 < n_out_valid && col < n_in) {
-        atomicAdd(&gW[r1 * n_in + col], d[2]);
-        atomicAdd(&gW[r1 * n_in + col + 1], d[3]);
+        atomicAdd(&gW[r1 * ld + col], d[2]);
+        atomicAdd(&gW[r1 * ld + col + 1], d[3]);
       }
     }
   }
@@ -316,7 +333,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   load_weights(S.w, pb, pf);
-  for (int i = threadIdx.x; i < NP; i += blockDim.x) S.grad[i] = 0.0f;
+  for (int i = threadIdx.x; i < NPS; i += blockDim.x) S.grad[i] = 0.0f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   WarpSmem* ws = &S.warp[warp];
   for (int i = lane; i < H * (16 + PK); i += 32) (&ws->dzt[0][0])[i] = __float2bfloat16(0.0f);
@@ -356,8 +373,8 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
     __syncwarp();
     store_dzt(ws, dz4, 1);
     __syncwarp();
-    accumulate_dw(ws, ws->at[2], 1, 8, OUT, H, &S.grad[OW4]);
-    accumulate_db(dz4, 1, OUT, &S.grad[OB4]);
+    accumulate_dw(ws, ws->at[2], 1, 8, OUT, H, GLD, &S.grad[SW4]);
+    accumulate_db(dz4, 1, OUT, &S.grad[SB4]);
     // dA3 = dZ4 W4: A operand from the dZ4 fragment (K padded 8 -> 16)
     uint32_t a[4][4];
     a[0][0] = pack2(dz4[0][0], dz4[0][1]);
@@ -383,10 +400,10 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
       __syncwarp();
       store_dzt(ws, dz, 8);
       __syncwarp();
-      float* gW = layer == 2 ? &S.grad[OW3] : layer == 1 ? &S.grad[OW2] : &S.grad[OW1];
-      float* gb = layer == 2 ? &S.grad[OB3] : layer == 1 ? &S.grad[OB2] : &S.grad[OB1];
-      if (layer > 0) accumulate_dw(ws, ws->at[layer - 1], 4, 8, H, H, gW);
-      else accumulate_dw(ws, ws->xt, 4, 1, H, IN, gW);
+      float* gW = layer == 2 ? &S.grad[SW3] : layer == 1 ? &S.grad[SW2] : &S.grad[SW1];
+      float* gb = layer == 2 ? &S.grad[SB3] : layer == 1 ? &S.grad[SB2] : &S.grad[SB1];
+      if (layer > 0) accumulate_dw(ws, ws->at[layer - 1], 4, 8, H, H, GLD, gW);
+      else accumulate_dw(ws, ws->xt, 4, 1, H, IN, IN, gW);
       accumulate_db(dz, 8, H, gb);
       if (layer > 0) {
 #pragma unroll
@@ -404,8 +421,10 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
   for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
   if (lane == 0 && loss) atomicAdd(loss, loss_acc);
   __syncthreads();
-  for (int i = threadIdx.x; i < NP; i += blockDim.x)
-    if (S.grad[i] != 0.0f) atomicAdd(&grad[i], S.grad[i]);
+  for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+    const float v = S.grad[padded(i)];
+    if (v != 0.0f) atomicAdd(&grad[i], v);
+  }
 }
 
 __global__ void __launch_bounds__(THREADS) k_mlp_infer(const __nv_bfloat16* pb, const float* pf,
