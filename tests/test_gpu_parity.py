@@ -339,6 +339,46 @@ def test_table_edges_and_size_limits(Q, oracle):
     assert err.value.code == -4
 
 
+def test_per_lane_failure_statuses(Q):
+    """Per-lane failures end that lane with a status while the call succeeds
+    and every other lane's outcome is unchanged: a NaN in the state gives
+    FAIL_NAN, a step size below 2^-49 of the time (t = 1e15, h = 1e-3)
+    FAIL_HMIN, and a cap of 20 attempts FAIL_MAXSTEPS with class FAIL.
+    FP64 one-thread-per-lane and persistent launches, and the FP32
+    integrator."""
+    import torch
+    wl = W.plain_h2_ca(per_b=8)
+    for prec, persistent in [(64, False), (64, True), (32, True)]:
+        kw = W.INTEG_FP64 if prec == 64 else W.INTEG_FP32
+        integ = Q.make_integ(**kw, persistent=persistent, precision=prec)
+        ref, _, _, _ = Q.run_workload(wl, integ, finalize=False)
+        torch.cuda.synchronize()
+        r = ref.host()
+        b = Q.Batch.empty(wl.n, "cuda", sys_id=wl.sys_id, cell=wl.cell)
+        Q.init_states(wl.systems, b, wl.E, wl.b, wl.v, wl.j, wl.R0, wl.seed, wl.id_offset)
+        b.y[0][3] = float("nan")
+        b.f64["t"][5] = 1e15
+        b.f64["h"][5] = 1e-3
+        Q.run_batch(wl.systems, b, integ)
+        torch.cuda.synchronize()
+        g = b.host()
+        assert g["status"][3] == Q.LANE["FAIL_NAN"], (prec, persistent, g["status"][3])
+        assert g["status"][5] == Q.LANE["FAIL_HMIN"], (prec, persistent, g["status"][5])
+        assert g["cls"][3] == Q.CLS["FAIL"] and g["cls"][5] == Q.CLS["FAIL"]
+        other = np.ones(wl.n, bool)
+        other[[3, 5]] = False
+        for k in ("status", "cls", "nsteps", "vt", "jt"):
+            assert np.array_equal(g[k][other], r[k][other]), (prec, persistent, k)
+        assert np.array_equal(g["y"][other], r["y"][other])
+        cap = Q.make_integ(**kw, persistent=persistent, precision=prec, max_steps=20)
+        c, _, _, _ = Q.run_workload(wl, cap, finalize=False)
+        torch.cuda.synchronize()
+        h = c.host()
+        assert np.all(h["status"] == Q.LANE["FAIL_MAXSTEPS"]), (prec, persistent)
+        assert np.all(h["cls"] == Q.CLS["FAIL"])
+        assert np.all(h["nsteps"] + h["nrej"] == 20)
+
+
 def test_mixed_potentials_parity(Q, oracle):
     """Buckingham / LJ(12,6) / LJ(8,6) Ca-H with mixed (v, j): outcome classes
     agree for >= 99% of lanes."""
