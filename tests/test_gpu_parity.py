@@ -173,6 +173,46 @@ def test_adaptive_plain_study_parity(Q, oracle):
     assert np.all(g["cls"][sep] == 0)
 
 
+def test_tiny_batch_field_by_field(Q, oracle):
+    """32 lanes run by the oracle one by one, every per-lane output compared:
+    18 lanes of the plain study (b = 0, 3, 6 bohr: direct collisions) and 14
+    of the sweep (its lowest and highest energies).  Integers (status,
+    class, accepted and rejected steps, v_t, j_t) agree exactly on every
+    plain-study lane and on every sweep lane whose two step sequences
+    coincide (low-energy lanes that form long-lived complexes separate
+    chaotically, and at least 10 of the 14 must coincide).  The GPU's
+    step-size controller takes its error norm in FP32 from 20-bit magnitudes,
+    so its step sizes differ from the oracle's FP64 ones by ~1e-6 relative:
+    the same steps are accepted, but at slightly different times.  Hence the
+    stop time agrees to 1e-6, the state there to 1e-4, v' and j' to 1e-5,
+    the Gaussian weight (whose slope is 1/sigma_GB^2 ~ 550 in v') to 1e-3,
+    and the energy error, a property of the integration, to 1e-12 absolute
+    (measured: 1.0e-7, 2.5e-5, 6.7e-7, 6.2e-7, 7.9e-5, 1.8e-14)."""
+    sw = W.sweep_h2_ca(per_cell=4)
+    pick = np.r_[np.arange(0, 7), np.arange(sw.n - 7, sw.n)]
+    cases = [W.plain_h2_ca(per_b=6, b_grid=(0.0, 3.0, 6.0)), sw.take(pick)]
+    worst = {}
+    for c, wl in enumerate(cases):
+        batch, g, hist, cells, groups, st, res = _adaptive_pair(Q, oracle, wl)
+        same = (g["nsteps"] == res["nsteps"]) & (g["nrej"] == res["nrej"])
+        assert same.all() if c == 0 else same.sum() >= 10, (wl.name, g["nsteps"], res["nsteps"])
+        for k in ("status", "cls", "vt", "jt"):
+            assert np.array_equal(g[k][same], res[k][same]), (wl.name, k)
+        ok = same & (g["status"] == 2)
+        dev = {"t": np.abs(g["t"] - res["t"]) / res["t"],
+               "y": np.max(np.abs(g["y"] - st["y"]) / (np.abs(st["y"]) + 1.0), axis=1),
+               "vprime": np.abs(g["vprime"] - res["vprime"]),
+               "jprime": np.abs(g["jprime"] - res["jprime"]),
+               "dE": np.abs(g["dE"] - res["dE"]),
+               "gbw": np.abs(g["gbw"] - res["gbw"]) / np.maximum(np.abs(res["gbw"]), 1e-300)}
+        for k, d in dev.items():
+            worst[k] = max(worst.get(k, 0.0), float(np.max(d[ok])) if ok.any() else 0.0)
+    print("\nlargest deviations: " + ", ".join(f"{k} {v:.1e}" for k, v in worst.items()))
+    assert worst["t"] < 1e-6 and worst["y"] < 1e-4
+    assert worst["vprime"] < 1e-5 and worst["jprime"] < 1e-5
+    assert worst["dE"] < 1e-12 and worst["gbw"] < 1e-3
+
+
 def test_persistent_equals_plain(Q):
     """The refill-queue launch computes every lane exactly as the
     one-thread-per-lane launch does (bit-identical outputs)."""
