@@ -656,3 +656,42 @@ def test_gb_distribution_normalisation_and_integer_case(oracle):
         for v in range(12):
             ncv = np.sum(sel & (cls == c) & (vt == v))
             assert P[c, v] == pytest.approx(ncv / (nb + Nd / peak), rel=1e-9, abs=1e-15)
+
+
+def test_adaptive_controller_matches_scipy_rk45(oracle):
+    """The oracle's step-size control (starting step, error norm, factors,
+    no growth after a rejection) restates SciPy's RK45, which the paper uses
+    (Sec. 3.2): stepping scipy.integrate.RK45 itself on the oracle's
+    Hamilton equations from the same initial state, with the stop rules out
+    of the way (r_stop far away, t_max = 800 atomic time units), gives the
+    same number of accepted steps, the same end time up to rounding-level
+    step-size differences, and the same state there within the tolerance."""
+    from scipy.integrate import RK45
+    s = oracle.system_from_spec(W.SYS_H2_CA_MORSE)
+    for E, b, v, j, rtol, atol in [(0.10, 1.5, 0, 0, 1e-10, 1e-12), (0.05, 4.0, 2, 5, 1e-8, 1e-10)]:
+        st = oracle.init([s], np.zeros(1, np.int32), [E], [b], [v], [j], 30.0, 3)
+        y0 = st["y"][0].copy()
+        t_stop = 800.0 / st["t_scale"][0]          # t_max = 800 atomic time units
+        integ = oracle.make_integ(rtol=rtol, atol=atol, r_stop=1e6, t_stop=t_stop)
+        y = st["y"].copy()
+        res = oracle.run_adaptive([s], np.zeros(1, np.int32), integ, y, st["t_scale"], st["E0"],
+                                  st["status"])
+        assert res["status"][0] == 3                  # stopped by t_max
+        t_end, n_acc = res["t"][0], int(res["nsteps"][0])
+        solver = RK45(lambda t, x: oracle.rhs(s, x), 0.0, y0, t_bound=1e9, rtol=rtol, atol=atol)
+        n = 0
+        while solver.t < 800.0:
+            solver.step()
+            assert solver.status == "running"
+            n += 1
+        assert n == n_acc, (n, n_acc)
+        # the error estimate is a cancellation (5th- minus 4th-order
+        # solution), so its relative rounding error is ~eps / rtol ~ 1e-6 and
+        # two valid summation orders give step sizes that differ at that
+        # level: the times agree to ~1e-8, and the states at the oracle's end
+        # time (SciPy's dense output of its last step) to the tolerance
+        dt = abs(solver.t - t_end) / t_end
+        yi = solver.dense_output()(t_end)
+        dy = np.max(np.abs(yi - y[0]) / (np.abs(y[0]) + 1.0))
+        print(f"\nrtol {rtol:g}: {n} accepted steps both; |dt|/t {dt:.1e}, state {dy:.1e}")
+        assert dt < 1e-7 and dy < 100 * rtol
