@@ -33,31 +33,31 @@ if ROOT not in sys.path:
 
 # FP64 floating-point operations per attempted integrator step of the Morse
 # kernel: 2 dfma + dmul + dadd, from ncu sass counters on the profile case
-# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 540 DFMA,
-# 215 DMUL, 19 DADD per lane-step, six right-hand sides included.  The FP64
-# pipe issues 540 + 215 + 19 = 774 instructions per step; the DFMA-chain
+# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 486 DFMA,
+# 176 DMUL, 1 DADD per lane-step, six right-hand sides included.  The FP64
+# pipe issues 486 + 176 + 1 = 663 instructions per step; the DFMA-chain
 # peak runs one DFMA (2 FLOP) per pipe slot, so pipe_frac below is the
 # fraction of the pipe's instruction rate the kernel uses.
-FP64_FLOP_PER_STEP = 1314
-FP64_INSTR_PER_STEP = 774
+FP64_FLOP_PER_STEP = 1149
+FP64_INSTR_PER_STEP = 663
 # FP32 floating-point operations per attempted step of the FP32 Morse kernel
 # (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
-# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 404 FFMA,
-# 226 FMUL, 39 FADD per lane-step); it also issues one DADD (the time).  The
-# kernel is bound by instruction issue: 963 thread instructions per step
+# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 392 FFMA,
+# 225 FMUL, 39 FADD per lane-step); it also issues one DADD (the time).  The
+# kernel is bound by instruction issue: 946 thread instructions per step
 # (all pipes), so issue_frac below is the fraction of the SMs' issue rate
 # (4 warp instructions per SM per cycle) it uses.
-FP32_FLOP_PER_STEP = 1074
-FP32_THREAD_INSTR_PER_STEP = 963
+FP32_FLOP_PER_STEP = 1049
+FP32_THREAD_INSTR_PER_STEP = 946
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the FP64 profile case (1,197,312 B for 3,840
-# lanes in 30 blocks) less the 30 blocks' 16 KB exponential tables (a fixed
-# cost per resident block, ~5 MB for a full-size launch), per lane: the state
-# is loaded once and stored once, everything else is in registers.
-DRAM_BYTES_PER_LANE = (1197312 - 30 * 16384) / 3840
-# The same for the FP32 kernel (561,152 B read, no table): its state is
+# dram__bytes_write.sum of the FP64 profile case (683,520 B read, nothing
+# written back during the launch, for 3,840 lanes), per lane: the state is
+# loaded once, everything else is in registers; the 16 KB exponential table
+# is read from DRAM once and served from L2 to the other blocks.
+DRAM_BYTES_PER_LANE = 683520 / 3840
+# The same for the FP32 kernel (560,896 B read, no table): its state is
 # loaded as (value, compensation) pairs from the same FP64 arrays.
-DRAM_BYTES_PER_LANE_FP32 = 561152 / 3840
+DRAM_BYTES_PER_LANE_FP32 = 560896 / 3840
 
 
 def parse():
@@ -388,7 +388,7 @@ def run_ours(args):
                                f"(qcams_fma_peak), this run",
                 "traffic": ((DRAM_BYTES_PER_LANE if args.precision == 64 else DRAM_BYTES_PER_LANE_FP32)
                             * wl.n if args.workload == "sweep" else None),
-                "traffic_note": "ncu dram bytes of the 3,840-lane profile case (less its per-block exp tables) scaled by lanes"}
+                "traffic_note": "ncu dram bytes of the 3,840-lane profile case scaled by lanes"}
     if args.workload in ("sweep", "plain"):
         # FLOP counts are those of the Morse kernel (H2 + Ca systems)
         ach = flop_per_step * steps_per_launch / (avg_integ_ms * 1e-3)

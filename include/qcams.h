@@ -87,7 +87,9 @@ typedef struct {
                      LJ r_scale: a length near the well (the paper's "re
                      guess"), used to bound root searches.  Buckingham
                      r_max_guess: a length near the short-range maximum
-                     (the paper's "max"). */
+                     (the paper's "max").  Morse pairs need alpha re < 700
+                     (QCAMS_E_INVALID otherwise): e^{alpha (re - r)} stays
+                     finite down to r = 0. */
 } qcams_pair;
 
 typedef struct {
@@ -546,6 +548,20 @@ int qcams_fma_peak(int32_t precision, double* flops_per_s, void* cuda_stream);
  */
 int qcams_debug_exp(const double* x, double* out_table, double* out_cuda, int64_t n,
                     void* cuda_stream);
+
+/*
+ * Diagnostic (test support): the elementary functions of the integrator's
+ * Morse force law (Sec. 3.2 item 1, V = De (1 - e^{-alpha (r - re)})^2 - De)
+ * on n device squared distances s[i]:
+ *   out_rinv[i] = 1/sqrt(s[i])   (FP32 hardware estimate refined in FP64;
+ *                                 NaN outside 2^-126 <= s < 2^128),
+ *   out_arg[i]  = x = alpha_re - alpha r,  r = s[i] out_rinv[i],
+ *   out_exp[i]  = e^x            (table method with the index rounded in FP32).
+ * alpha > 0, 0 < alpha_re < 700, else QCAMS_E_INVALID.  Device arrays of
+ * length n, caller-owned.  Asynchronous.
+ */
+int qcams_debug_force_math(const double* s, double alpha, double alpha_re, double* out_rinv,
+                           double* out_arg, double* out_exp, int64_t n, void* cuda_stream);
 
 /* Device properties used for launch shapes: SM count and CC. */
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);

@@ -80,11 +80,15 @@ int make_devpair(const qcams_pair& in, DevPair* out) {
   switch (in.kind) {
     case QCAMS_MORSE:
       if (!finite_pos(p[0]) || !finite_pos(p[1]) || !finite_pos(p[2])) return QCAMS_E_INVALID;
+      // the integrator's exponential takes arguments alpha (re - r) < 700
+      if (!(p[2] * p[1] < 700.0)) return QCAMS_E_INVALID;
       out->c0 = p[2];
       out->c1 = p[2] * p[1];
       out->c2 = 2.0 * p[2] * p[0];
       out->c3 = p[0];
       out->r_scale = p[1];
+      out->ef0 = (float)out->c0;
+      out->ef1 = (float)out->c1;
       return QCAMS_OK;
     case QCAMS_LJ: {
       double m = p[0], n = p[1];
@@ -108,6 +112,7 @@ int make_devpair(const qcams_pair& in, DevPair* out) {
       out->c3 = 6.0 * p[2];
       out->c4 = p[2];
       out->r_scale = p[3] > 0 ? p[3] : 1.0;
+      out->ef0 = (float)out->c1;
       return QCAMS_OK;
     default:
       return QCAMS_E_INVALID;
@@ -1027,6 +1032,17 @@ int qcams_debug_exp(const double* x, double* out_table, double* out_cuda, int64_
   if ((rc = check_device()) != QCAMS_OK) return rc;
   if (n == 0) return QCAMS_OK;
   return cuda_status(launch_exp_check(x, out_table, out_cuda, n, (cudaStream_t)cuda_stream));
+}
+
+int qcams_debug_force_math(const double* s, double alpha, double alpha_re, double* out_rinv,
+                           double* out_arg, double* out_exp, int64_t n, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!s || !out_rinv || !out_arg || !out_exp))) return QCAMS_E_INVALID;
+  if (!(alpha > 0.0) || !(alpha_re > 0.0) || !(alpha_re < 700.0)) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  if (n == 0) return QCAMS_OK;
+  return cuda_status(launch_force_math_check(s, alpha, alpha_re, out_rinv, out_arg, out_exp, n,
+                                             (cudaStream_t)cuda_stream));
 }
 
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor) {

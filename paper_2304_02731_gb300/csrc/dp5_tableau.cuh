@@ -53,6 +53,19 @@ __host__ __device__ constexpr double dpEA(int q) {
   return acc;
 }
 
+// Entries of A^2 and e^T A that are zero in exact arithmetic.  (A^2)_{s,q}
+// needs q < j < s, so it vanishes for q >= s - 1.  (A^2)_{7,2} = sum_j b_j a_j2
+// = b_2 (1 - c_2) = 0, since the last row of A is b and the tableau satisfies
+// sum_i b_i a_ij = b_j (1 - c_j); (e^T A)_2 = 0 as well (both checked in
+// rational arithmetic).  The double sums above leave rounding residues of
+// about 1e-16 there, so the tables store exact zeros and the integrators
+// skip those terms at compile time.
+__host__ __device__ constexpr bool dpA2Zero(int s, int q) { return q >= s - 1 || (s == 7 && q == 2); }
+__host__ __device__ constexpr bool dpEAZero(int q) { return q == 2 || q >= 7; }
+static_assert(dpA2(7, 2) < 1e-15 && dpA2(7, 2) > -1e-15, "(A^2)_{7,2} is a rounding residue");
+static_assert(dpEA(2) < 1e-15 && dpEA(2) > -1e-15, "(e^T A)_2 is a rounding residue");
+static_assert(dpA2(7, 1) > 0.09 && dpEA(3) < -6e-3, "nonzero neighbours stay nonzero");
+
 struct RknTab {
   double a2[8][8];  // (A^2)_{s,q}, s,q 1-based
   double c[8];
@@ -66,8 +79,8 @@ __host__ __device__ constexpr RknTab make_rkn_tab() {
     t.c[s] = dpC(s);
     t.b[s] = dpB(s);
     t.e[s] = dpE(s);
-    t.ea[s] = dpEA(s);
-    for (int q = 1; q <= 7; ++q) t.a2[s][q] = dpA2(s, q);
+    t.ea[s] = dpEAZero(s) ? 0.0 : dpEA(s);
+    for (int q = 1; q <= 7; ++q) t.a2[s][q] = dpA2Zero(s, q) ? 0.0 : dpA2(s, q);
   }
   return t;
 }

@@ -26,14 +26,18 @@
 //    controller's error norm (magnitudes taken from the doubles' exponent and
 //    leading mantissa bits, ratios in FP32), the stop tests (integer compares
 //    of non-negative doubles) and the minimum-step test (exponent compare).
-//  * The Morse exponential is a table-driven exponential (Tang's method) with
-//    a 2048-entry table of 2^(j/2048) in shared memory: 8 FP64 instructions.
+//  * Each pair force takes 1/sqrt(s) and e^x (elem64.cuh): an FP32 hardware
+//    estimate finished in FP64, 3 FP64 instructions for the reciprocal
+//    square root and 5 for the exponential (Tang's table method, a 2048-entry
+//    table of 2^(j/2048) in shared memory, the table index rounded in FP32).
+//  * Stages 6 and 7 (c = 1) share rho + h v, and the tableau entries that are
+//    zero in exact arithmetic are skipped at compile time.
 #include <cuda_runtime.h>
 
 #include "qcams_device.cuh"
 #include "qcams_internal.h"
 #include "dp5_tableau.cuh"
-#include "texp.cuh"
+#include "elem64.cuh"
 
 namespace qcams {
 namespace {
@@ -73,21 +77,22 @@ constexpr unsigned FULL = 0xffffffffu;
 // ---------------------------------------------------------------------------
 template <bool MORSE>
 __device__ __forceinline__ double pair_u(const DevPair& q, double s, const double* __restrict__ T) {
-  const double ri = rsqrt(s);
+  float rf;   // FP32 estimate of r, for the exponential's table index
+  const double ri = rsqrt_seeded(s, rf);
   const double r = s * ri;
   if (MORSE) {
     // u = x (1 - x) / r, x = e^{-alpha (r - re)}; the factor 2 alpha De is in kf_morse
-    const double x = texp(fma(-q.c0, r, q.c1), T);
+    const double x = texp_hint(fma(-q.c0, r, q.c1), fmaf(-q.ef0, rf, q.ef1), T);
     return fma(-x, x, x) * ri;
   }
   // generic kernels (mixed systems): u = V'(r)/r with the table exponential
   if (q.kind == QCAMS_MORSE) {
-    const double x = texp(fma(-q.c0, r, q.c1), T);
+    const double x = texp_hint(fma(-q.c0, r, q.c1), fmaf(-q.ef0, rf, q.ef1), T);
     return q.c2 * fma(-x, x, x) * ri;
   }
   if (q.kind == QCAMS_BUCK) {
     const double ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-    return (q.c3 * ri6 * ri - q.c2 * texp(-q.c1 * r, T)) * ri;
+    return (q.c3 * ri6 * ri - q.c2 * texp_hint(-q.c1 * r, -q.ef0 * rf, T)) * ri;
   }
   return pot_g(q, ri, r);
 }
@@ -119,23 +124,35 @@ __device__ __forceinline__ void accel(const DevSys& S, const double* __restrict_
   a[5] = fma(h1, rbc2, h2 * rca2);
 }
 
-// Position of stage s (1-based, s >= 2).
-// The stage's coefficients h^2 (A^2)_{sq} are formed once per stage (s - 2
-// multiplies) rather than scaling each component's sum by h^2 (6 multiplies).
+// Position of stage s (1-based, s >= 2) from base = rho + h c_s v.
+// The stage's coefficients h^2 (A^2)_{sq} are formed once per stage rather
+// than scaling each component's sum by h^2 (6 multiplies); entries that are
+// zero in exact arithmetic are skipped (stage 2 has no acceleration term).
+template <int s>
+__device__ __forceinline__ void stage_x(const double* base, const double (*acc)[6], double hh,
+                                        double* x) {
+  double w[s > 2 ? s - 2 : 1];
+#pragma unroll
+  for (int q = 1; q <= s - 2; ++q) w[q - 1] = dpA2Zero(s, q) ? 0.0 : hh * kT.a2[s][q];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double xi = base[i];
+#pragma unroll
+    for (int q = 1; q <= s - 2; ++q)
+      if (!dpA2Zero(s, q)) xi = fma(w[q - 1], acc[q - 1][i], xi);
+    x[i] = xi;
+  }
+}
+// The same for stages 2-5 (c_s < 1), forming rho + h c_s v per component.
 template <int s>
 __device__ __forceinline__ void stage_x(const double* rho, const double* vel, const double (*acc)[6],
                                         double h, double hh, double* x) {
-  const double hc = h * kT.c[s];
-  double w[s > 2 ? s - 2 : 1];
+  static_assert(s >= 2 && s <= 5, "stages 6 and 7 share rho + h v");
+  const double hc = h * dpC(s);
+  double base[6];
 #pragma unroll
-  for (int q = 1; q <= s - 2; ++q) w[q - 1] = hh * kT.a2[s][q];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    double xi = fma(hc, vel[i], rho[i]);   // (A^2)_{2q} = 0: stage 2 has no acceleration term
-#pragma unroll
-    for (int q = 1; q <= s - 2; ++q) xi = fma(w[q - 1], acc[q - 1][i], xi);
-    x[i] = xi;
-  }
+  for (int i = 0; i < 6; ++i) base[i] = fma(hc, vel[i], rho[i]);
+  stage_x<s>(base, acc, hh, x);
 }
 
 // One Dormand-Prince step of size h from (rho, vel) with acc[0] = a(rho).
@@ -158,9 +175,12 @@ __device__ __forceinline__ void dp_step(const DevSys& S, const double* __restric
   accel<MORSE>(S, T, x, acc[3], s2);
   stage_x<5>(rho, vel, acc, h, hh, x);
   accel<MORSE>(S, T, x, acc[4], s2);
-  stage_x<6>(rho, vel, acc, h, hh, x);
+  double base[6];   // c_6 = c_7 = 1
+#pragma unroll
+  for (int i = 0; i < 6; ++i) base[i] = fma(h, vel[i], rho[i]);
+  stage_x<6>(base, acc, hh, x);
   accel<MORSE>(S, T, x, acc[5], s2);
-  stage_x<7>(rho, vel, acc, h, hh, xn);
+  stage_x<7>(base, acc, hh, xn);
   accel<MORSE>(S, T, xn, acc[6], s2);
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -174,7 +194,8 @@ __device__ __forceinline__ void dp_step(const DevSys& S, const double* __restric
     ev[i] = e;
     double ea = kT.ea[1] * acc[0][i];
 #pragma unroll
-    for (int q = 2; q <= 6; ++q) ea = fma(kT.ea[q], acc[q - 1][i], ea);
+    for (int q = 2; q <= 6; ++q)
+      if (!dpEAZero(q)) ea = fma(kT.ea[q], acc[q - 1][i], ea);
     er[i] = ea;
   }
 }
@@ -515,6 +536,24 @@ __global__ void k_exp_check(const double* x, double* mine, double* ref, long lon
   ref[i] = exp(x[i]);
 }
 
+// The integrator's pair-force elementary functions on n squared distances s
+// of one Morse pair (alpha = c0, alpha re = c1): 1/sqrt(s), the exponent's
+// argument x = c1 - c0 r and e^x, exactly as the force law forms them.
+__global__ void k_force_math_check(const double* s, double c0, double c1, float c0f, float c1f,
+                                   double* ri_out, double* x_out, double* e_out, long long n) {
+  __shared__ double sT[kExpTableSize];
+  load_exp_table(sT);
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float rf;
+  const double si = s[i];
+  const double ri = rsqrt_seeded(si, rf);
+  const double x = fma(-c0, si * ri, c1);
+  ri_out[i] = ri;
+  x_out[i] = x;
+  e_out[i] = texp_hint(x, fmaf(-c0f, rf, c1f), sT);
+}
+
 bool all_morse(const SysSet& s) {
   for (int k = 0; k < s.n; ++k)
     for (int p = 0; p < 3; ++p)
@@ -586,6 +625,13 @@ cudaError_t launch_variant(int v, const SysSet& sys, const DevShape* shapes,
 cudaError_t launch_exp_check(const double* x, double* mine, double* ref, long long n,
                              cudaStream_t st) {
   k_exp_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, mine, ref, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_force_math_check(const double* s, double c0, double c1, double* ri,
+                                    double* x, double* e, long long n, cudaStream_t st) {
+  k_force_math_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, c0, c1, (float)c0,
+                                                                  (float)c1, ri, x, e, n);
   return cudaGetLastError();
 }
 

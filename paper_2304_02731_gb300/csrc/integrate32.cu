@@ -36,8 +36,8 @@ __host__ __device__ constexpr RknTabF make_rkn_tab_f() {
     f.c[s] = (float)dpC(s);
     f.b[s] = (float)dpB(s);
     f.e[s] = (float)dpE(s);
-    f.ea[s] = (float)dpEA(s);
-    for (int q = 1; q <= 7; ++q) f.a2[s][q] = (float)dpA2(s, q);
+    f.ea[s] = dpEAZero(s) ? 0.0f : (float)dpEA(s);
+    for (int q = 1; q <= 7; ++q) f.a2[s][q] = dpA2Zero(s, q) ? 0.0f : (float)dpA2(s, q);
   }
   return f;
 }
@@ -155,20 +155,20 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
   float x[6], s2[3];
 #define QCAMS_STAGE(sIdx)                                                            \
   {                                                                                  \
-    const float hc = h * kTf.c[sIdx];                                                \
+    const float hc = h * (float)dpC(sIdx); /* folded: c_6 = 1 */                     \
     float w[(sIdx) - 2];                                                             \
     _Pragma("unroll") for (int q = 1; q <= (sIdx) - 2; ++q)                          \
         w[q - 1] = hh * kTf.a2[sIdx][q];                                             \
     _Pragma("unroll") for (int i = 0; i < 6; ++i) {                                  \
       float xi = fmaf(hc, L.vel[i], L.rho[i]);                                       \
       _Pragma("unroll") for (int q = 1; q <= (sIdx) - 2; ++q)                        \
-          xi = fmaf(w[q - 1], L.acc[q - 1][i], xi);                                  \
+          if (!dpA2Zero(sIdx, q)) xi = fmaf(w[q - 1], L.acc[q - 1][i], xi);          \
       x[i] = xi;                                                                     \
     }                                                                                \
     accel<MORSE>(S, x, L.acc[(sIdx) - 1], s2);                                       \
   }
   {  // stage 2: (A^2)_{2q} = 0, no acceleration term
-    const float hc = h * kTf.c[2];
+    const float hc = h * (float)dpC(2);
 #pragma unroll
     for (int i = 0; i < 6; ++i) x[i] = fmaf(hc, L.vel[i], L.rho[i]);
     accel<MORSE>(S, x, L.acc[1], s2);
@@ -185,7 +185,8 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
   for (int i = 0; i < 6; ++i) {
     float sum = 0.0f;
 #pragma unroll
-    for (int q = 1; q <= 5; ++q) sum = fmaf(kTf.a2[7][q], L.acc[q - 1][i], sum);
+    for (int q = 1; q <= 5; ++q)
+      if (!dpA2Zero(7, q)) sum = fmaf(kTf.a2[7][q], L.acc[q - 1][i], sum);
     const float d = fmaf(hh, sum, h * L.vel[i]);
     yr[i] = d - L.crho[i];
     x[i] = L.rho[i] + yr[i];
@@ -204,7 +205,8 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
     ev[i] = h * e;
     float ea = kTf.ea[1] * L.acc[0][i];
 #pragma unroll
-    for (int q = 2; q <= 6; ++q) ea = fmaf(kTf.ea[q], L.acc[q - 1][i], ea);
+    for (int q = 2; q <= 6; ++q)
+      if (!dpEAZero(q)) ea = fmaf(kTf.ea[q], L.acc[q - 1][i], ea);
     er[i] = hh * ea;
   }
   float sum = 0.0f;

@@ -27,6 +27,10 @@ struct DevPair {
   //   Buck:  c0 = A, c1 = B, c2 = A B, c3 = 6 C6, c4 = C6
   double c0, c1, c2, c3, c4;
   double r_scale;  // a length near the well (root-search brackets)
+  // FP32 copies of the exponent's coefficients, for the FP32 estimate of the
+  // argument that the integrator's exponential rounds to its table index:
+  //   Morse: ef0 = alpha, ef1 = alpha re (x = ef1 - ef0 r);  Buck: ef0 = B (x = -B r)
+  float ef0, ef1;
 };
 
 struct DevSys {

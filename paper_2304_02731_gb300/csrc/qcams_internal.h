@@ -40,6 +40,11 @@ struct IntegParams {
 cudaError_t launch_exp_check(const double* x, double* mine, double* ref, long long n,
                              cudaStream_t st);
 
+// Diagnostic: the integrator's pair-force 1/sqrt(s), exponent argument and
+// exponential for one Morse pair (integrate.cu; used by the accuracy test).
+cudaError_t launch_force_math_check(const double* s, double c0, double c1, double* ri,
+                                    double* x, double* e, long long n, cudaStream_t st);
+
 // Validation and launch helpers defined in api.cu.
 int prepare_run(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
                 const qcams_batch* batch, SysSet* ss, IntegParams* ip, DevBatch* d);

@@ -36,7 +36,7 @@ GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
 EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
            "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
-           "qcams_debug_exp", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
+           "qcams_debug_exp", "qcams_debug_force_math", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
            "qcams_mlp_features", "qcams_mlp_fit_standardizer", "qcams_mlp_grad",
            "qcams_mlp_train_step", "qcams_mlp_train", "qcams_mlp_infer", "qcams_build_proposal",
            "qcams_sample_proposal", "qcams_rate_constants", "qcams_gb_distribution"]
@@ -142,6 +142,7 @@ def lib():
                 "qcams_shutdown": (C.c_int, []),
                 "qcams_run_batch_noalloc": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
                 "qcams_debug_exp": (C.c_int, [V, V, V, I64, V]),
+                "qcams_debug_force_math": (C.c_int, [V, D, D, V, V, V, I64, V]),
                 "qcams_autotune": (C.c_int, [P(System), I32, P(Integ), P(CBatch), I64,
                                              P(TuneResult), P(I32), P(Integ), V]),
                 "qcams_mlp_init": (C.c_int, [P(CMLP), C.c_uint64, V]),
@@ -432,6 +433,17 @@ def autotune(systems, sample: Batch, integ: Integ, max_attempts: int = 1500, str
                 resident_blocks=r.resident_blocks, ms=r.ms, lane_steps_per_s=r.lane_steps_per_s)
            for r in res[:nres.value]]
     return best, out
+
+
+def debug_force_math(s: torch.Tensor, alpha: float, alpha_re: float, stream=None):
+    """qcams_debug_force_math: (1/sqrt(s), x = alpha_re - alpha r, e^x) as the
+    integrator's Morse force law forms them, for the device tensor s."""
+    s = s.to(torch.float64).contiguous()
+    ri, x, e = torch.empty_like(s), torch.empty_like(s), torch.empty_like(s)
+    _check(lib().qcams_debug_force_math(s.data_ptr(), float(alpha), float(alpha_re),
+                                        ri.data_ptr(), x.data_ptr(), e.data_ptr(), s.numel(),
+                                        _stream(stream)), "qcams_debug_force_math")
+    return ri, x, e
 
 
 def debug_exp(x: torch.Tensor, stream=None):

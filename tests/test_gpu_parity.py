@@ -447,6 +447,43 @@ def test_table_exp_matches_cuda_exp(Q):
     assert torch.all(m2 > 0) and torch.all(m2 < 1e-303)
 
 
+def test_force_law_rsqrt_and_exp_accuracy(Q):
+    """The pair force's 1/sqrt(s) (an FP32 hardware estimate finished by one
+    FP64 series step) is within 1 ulp of the exact value over the FP32 normal
+    range and NaN outside it; its e^x (table method, index rounded in FP32,
+    reduction constant ln2/N without its tail) is within
+    4e-16 + 4e-17 |x| relative of exp of the same argument.  The bound adds
+    the dropped tail (|x| L2/L = 3.34e-17 |x|), the cubic's truncation at
+    |r| <= 0.62 ln2/N (8.3e-17) and two roundings (2.2e-16)."""
+    import torch
+    g = torch.Generator().manual_seed(3)
+    s = torch.cat([10 ** (torch.rand(1_000_000, generator=g, dtype=torch.float64)
+                          * math.log10(2500 / 0.03) + math.log10(0.03)),
+                   torch.linspace(0.05, 2500.0, 200_001, dtype=torch.float64)])
+    for alpha, alpha_re in [(1.0282, 1.0282 * 1.4011), (0.85, 0.85 * 3.79), (2.2, 4.4)]:
+        ri, x, e = (t.cpu().numpy() for t in Q.debug_force_math(s.cuda(), alpha, alpha_re))
+        sn = s.numpy()
+        exact = 1 / np.sqrt(sn.astype(np.longdouble))
+        ulps = np.abs(ri - exact) / np.spacing(exact.astype(np.float64))
+        ex = np.exp(x.astype(np.longdouble))
+        rel = np.abs(e - ex) / ex
+        ratio = rel / (4e-16 + 4e-17 * np.abs(x))
+        print(f"\nalpha {alpha}: 1/sqrt(s) max {float(ulps.max()):.3f} ulp; "
+              f"e^x max rel {float(rel.max()):.2e} at |x| <= {np.abs(x).max():.0f}, "
+              f"{float(ratio.max()):.3f} of the bound")
+        assert float(ulps.max()) <= 1.0
+        assert float(ratio.max()) <= 1.0
+        r = np.sqrt(sn)
+        assert np.all(np.abs(x - (alpha_re - alpha * r)) <= 1e-15 * (1 + alpha * r))
+    wide = torch.tensor([1e-37, 1e-30, 1e-10, 3.0, 1e10, 1e30, 3e38], dtype=torch.float64)
+    ri, _, _ = (t.cpu().numpy() for t in Q.debug_force_math(wide.cuda(), 1.0, 1.4))
+    exact = 1 / np.sqrt(wide.numpy().astype(np.longdouble))
+    assert np.all(np.abs(ri - exact) <= np.spacing(exact.astype(np.float64)))
+    bad = torch.tensor([0.0, 1e-300, 1e-40, 1e300, math.inf, math.nan, -1.0], dtype=torch.float64)
+    ri, x, e = Q.debug_force_math(bad.cuda(), 1.0, 1.4)
+    assert torch.isnan(ri).all().item()
+
+
 def test_autotune_restores_sample_and_shapes_agree(Q):
     """The autotuner leaves its sample untouched, and every launch shape
     integrates each lane identically (bit-for-bit)."""
