@@ -32,12 +32,18 @@
 //    table of 2^(j/2048) in shared memory, the table index rounded in FP32).
 //  * Stages 6 and 7 (c = 1) share rho + h v, and the tableau entries that are
 //    zero in exact arithmetic are skipped at compile time.
+//  * Linear combinations that do not need an FP64 result run as float-float
+//    compensated dot products on the FP32 / integer pipes (ff.cuh): the
+//    acceleration corrections of stages 4-6 (one DADD each onto the FP64
+//    base) and the embedded error estimate.  The new state (stage 7, v_n+1)
+//    keeps its FP64 sums.
 #include <cuda_runtime.h>
 
 #include "qcams_device.cuh"
 #include "qcams_internal.h"
 #include "dp5_tableau.cuh"
 #include "elem64.cuh"
+#include "ff.cuh"
 
 namespace qcams {
 namespace {
@@ -59,12 +65,35 @@ __device__ __forceinline__ float signed_f(double x) {
   const float m = mag_f(x, bad);
   return (__double2hiint(x) < 0) ? -m : m;
 }
+// |x| of an FP32 error estimate; sets `bad` for inf / NaN.
+__device__ __forceinline__ float err_mag(float x, unsigned& bad) {
+  bad |= ((__float_as_uint(x) & 0x7f800000u) == 0x7f800000u) ? 1u : 0u;
+  return fabsf(x);
+}
 // Order of non-negative doubles equals the order of their bit patterns.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 // Coefficients in the constant bank: a DFMA takes a constant-bank operand at
 // full rate, so indexing this table with compile-time indices costs nothing.
 __constant__ RknTab kT = make_rkn_tab();
+
+// The coefficients of the float-float sums as float pairs.
+struct RknTabFF {
+  FFc a2[8][8];
+  FFc e[8];
+  FFc ea[8];
+};
+__host__ __device__ constexpr RknTabFF make_rkn_tab_ff() {
+  RknTabFF f{};
+  const RknTab t = make_rkn_tab();
+  for (int s = 1; s <= 7; ++s) {
+    f.e[s] = make_ffc(t.e[s]);
+    f.ea[s] = make_ffc(t.ea[s]);
+    for (int q = 1; q <= 7; ++q) f.a2[s][q] = make_ffc(t.a2[s][q]);
+  }
+  return f;
+}
+__constant__ RknTabFF kTff = make_rkn_tab_ff();
 
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -143,11 +172,11 @@ __device__ __forceinline__ void stage_x(const double* base, const double (*acc)[
     x[i] = xi;
   }
 }
-// The same for stages 2-5 (c_s < 1), forming rho + h c_s v per component.
+// The same for stages 2 and 3 (c_s < 1), forming rho + h c_s v per component.
 template <int s>
 __device__ __forceinline__ void stage_x(const double* rho, const double* vel, const double (*acc)[6],
                                         double h, double hh, double* x) {
-  static_assert(s >= 2 && s <= 5, "stages 6 and 7 share rho + h v");
+  static_assert(s == 2 || s == 3, "stages 4-6 use stage_x_ff, 7 the FP64 form");
   const double hc = h * dpC(s);
   double base[6];
 #pragma unroll
@@ -155,30 +184,72 @@ __device__ __forceinline__ void stage_x(const double* rho, const double* vel, co
   stage_x<s>(base, acc, hh, x);
 }
 
+// Position of stage s = 4, 5, 6: base + h^2 sum_q (A^2)_{sq} a_q, the sum
+// as a float-float compensated dot product (FP32 / integer pipes) added to
+// the FP64 base with one DADD.  Its error, ~1e-13 h^2 |a|, reaches the step's
+// result through the stage force only, damped by (h omega)^3 below the FP64
+// rounding of the result; the 5th-order position (stage 7) and velocity
+// keep FP64 sums.
+template <int s>
+__device__ __forceinline__ void stage_x_ff(const double* base, const double (*acc)[6], float hhh,
+                                           float hhl, double* x) {
+  static_assert(s >= 4 && s <= 6, "stages 4-6");
+  float wh[s - 2], wl[s - 2];
+#pragma unroll
+  for (int q = 1; q <= s - 2; ++q) {
+    const FFc c = kTff.a2[s][q];
+    wh[q - 1] = __fmul_rn(hhh, c.hi);
+    wl[q - 1] = fmaf(hhh, c.hi, -wh[q - 1]) + fmaf(hhh, c.lo, hhl * c.hi);
+  }
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    float sm, cm, ah, al;
+    split_ff(acc[0][i], ah, al);
+    ff_dot_first(sm, cm, wh[0], wl[0], ah, al);
+#pragma unroll
+    for (int q = 2; q <= s - 2; ++q) {
+      split_ff(acc[q - 1][i], ah, al);
+      ff_dot_acc(sm, cm, wh[q - 1], wl[q - 1], ah, al);
+    }
+    x[i] = base[i] + ff_to_double(sm, cm);
+  }
+}
+
 // One Dormand-Prince step of size h from (rho, vel) with acc[0] = a(rho).
 // On return acc[1..6] hold the stage accelerations, xn / vn the 5th-order
 // solution (acc[6] = a(xn), FSAL), er / ev the embedded error estimates of
 // positions and velocities divided by h^2 and h (the error norm applies
 // those factors in FP32), s2 the squared pair distances at xn.
+//
+// The error estimates are sums of ~1e-9 |a| from terms of ~0.05 |a|; the
+// FP32 norm needs them to about 20 bits, so they are float-float
+// compensated dot products (relative error ~1e-6 where the norm is near 1,
+// the level of the norm's own 20-bit magnitudes) rather than FP64 sums.
 template <bool MORSE>
 __device__ __forceinline__ void dp_step(const DevSys& S, const double* __restrict__ T,
                                         const double* rho, const double* vel, double (*acc)[6],
-                                        double h, double* xn, double* vn, double* er, double* ev,
+                                        double h, double* xn, double* vn, float* er, float* ev,
                                         double* s2) {
   const double hh = h * h;
+  float hhh, hhl;
+  split_ff(hh, hhh, hhl);
   double x[6];
   stage_x<2>(rho, vel, acc, h, hh, x);
   accel<MORSE>(S, T, x, acc[1], s2);
   stage_x<3>(rho, vel, acc, h, hh, x);
   accel<MORSE>(S, T, x, acc[2], s2);
-  stage_x<4>(rho, vel, acc, h, hh, x);
-  accel<MORSE>(S, T, x, acc[3], s2);
-  stage_x<5>(rho, vel, acc, h, hh, x);
-  accel<MORSE>(S, T, x, acc[4], s2);
-  double base[6];   // c_6 = c_7 = 1
+  double base[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) base[i] = fma(h, vel[i], rho[i]);
-  stage_x<6>(base, acc, hh, x);
+  for (int i = 0; i < 6; ++i) base[i] = fma(h * dpC(4), vel[i], rho[i]);
+  stage_x_ff<4>(base, acc, hhh, hhl, x);
+  accel<MORSE>(S, T, x, acc[3], s2);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) base[i] = fma(h * dpC(5), vel[i], rho[i]);
+  stage_x_ff<5>(base, acc, hhh, hhl, x);
+  accel<MORSE>(S, T, x, acc[4], s2);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) base[i] = fma(h, vel[i], rho[i]);   // c_6 = c_7 = 1
+  stage_x_ff<6>(base, acc, hhh, hhl, x);
   accel<MORSE>(S, T, x, acc[5], s2);
   stage_x<7>(base, acc, hh, xn);
   accel<MORSE>(S, T, xn, acc[6], s2);
@@ -188,15 +259,19 @@ __device__ __forceinline__ void dp_step(const DevSys& S, const double* __restric
 #pragma unroll
     for (int q = 3; q <= 6; ++q) vb = fma(kT.b[q], acc[q - 1][i], vb);
     vn[i] = fma(h, vb, vel[i]);
-    double e = kT.e[1] * acc[0][i];
+    // (e^T A)_2 = e_2 = 0 and (e^T A)_7 = 0: a_2 never enters, a_7 only ev
+    float es, ec, rs, rc, ah, al;
+    split_ff(acc[0][i], ah, al);
+    ff_dot_first(es, ec, kTff.e[1].hi, kTff.e[1].lo, ah, al);
+    ff_dot_first(rs, rc, kTff.ea[1].hi, kTff.ea[1].lo, ah, al);
 #pragma unroll
-    for (int q = 3; q <= 7; ++q) e = fma(kT.e[q], acc[q - 1][i], e);
-    ev[i] = e;
-    double ea = kT.ea[1] * acc[0][i];
-#pragma unroll
-    for (int q = 2; q <= 6; ++q)
-      if (!dpEAZero(q)) ea = fma(kT.ea[q], acc[q - 1][i], ea);
-    er[i] = ea;
+    for (int q = 3; q <= 7; ++q) {
+      split_ff(acc[q - 1][i], ah, al);
+      ff_dot_acc(es, ec, kTff.e[q].hi, kTff.e[q].lo, ah, al);
+      if (!dpEAZero(q)) ff_dot_acc(rs, rc, kTff.ea[q].hi, kTff.ea[q].lo, ah, al);
+    }
+    ev[i] = es + ec;
+    er[i] = rs + rc;
   }
 }
 
@@ -318,11 +393,12 @@ __device__ void lane_store(const SysSet& sys, const DevBatch& B, int64_t i, cons
 // follows a rejection.  After an accepted step the stop rules are applied
 // (Sec. 3.1: r_stop while separating, or t >= t_max).
 //
-// Only the step itself (stages, update, error vector) is FP64.  The norm is
-// formed in FP32 from 20-bit magnitudes of the error, state and scale terms
-// (relative error < 1e-6, irrelevant to a step-size controller); accept /
-// reject is a select, so the warp does not diverge.  The minimum step is
-// checked by exponents: h fails below 8-16 ulp(t).
+// Only the step itself (stages, 5th-order update) is FP64; the error vector
+// comes as FP32 from float-float sums.  The norm is formed in FP32 from
+// 20-bit magnitudes of the state and scale terms (relative error < 1e-6,
+// irrelevant to a step-size controller); accept / reject is a select, so
+// the warp does not diverge.  The minimum step is checked by exponents: h
+// fails below 8-16 ulp(t).
 template <bool MORSE>
 __device__ __forceinline__ void lane_attempt(const SysSet& sys, const DevShape* shapes,
                                              const IntegParams& ip, const double* __restrict__ T,
@@ -336,7 +412,8 @@ __device__ __forceinline__ void lane_attempt(const SysSet& sys, const DevShape* 
       return;
     }
   }
-  double xn[6], vn[6], er[6], ev[6], s2[3];
+  double xn[6], vn[6], s2[3];
+  float er[6], ev[6];
   dp_step<MORSE>(S, T, L.rho, L.vel, L.acc, L.h, xn, vn, er, ev, s2);
   unsigned bad = 0, ignore = 0;
   float sum = 0.f;
@@ -346,11 +423,11 @@ __device__ __forceinline__ void lane_attempt(const SysSet& sys, const DevShape* 
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const float scr = fmaf(rt, fmaxf(mag_f(L.rho[i], ignore), mag_f(xn[i], ignore)), at);
-    const float qr = __fdividef(mag_f(er[i], bad) * hhf, scr);
+    const float qr = __fdividef(err_mag(er[i], bad) * hhf, scr);
     sum = fmaf(qr, qr, sum);
     const float scv = fmaf(rt, fmaxf(mag_f(L.vel[i], ignore), mag_f(vn[i], ignore)),
                            i < 3 ? atv0 : atv1);
-    const float qv = __fdividef(mag_f(ev[i], bad) * hf, scv);
+    const float qv = __fdividef(err_mag(ev[i], bad) * hf, scv);
     sum = fmaf(qv, qv, sum);
   }
   const float en2 = sum * (1.0f / 12.0f);
@@ -504,7 +581,8 @@ __global__ void __launch_bounds__(128) k_integrate_fixed(SysSet sys, IntegParams
       double t = B.t[i];
       const double h = ip.h_fixed;
       for (long long it = 0; it < ip.max_steps; ++it) {
-        double xn[6], vn[6], er[6], ev[6];
+        double xn[6], vn[6];
+        float er[6], ev[6];
         dp_step<MORSE>(S, sT, L.rho, L.vel, L.acc, h, xn, vn, er, ev, s2);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
@@ -685,8 +763,6 @@ cudaError_t integrate_variant_regs(int v, bool morse, int* regs) {
 }
 
 cudaError_t integrate_variant_occupancy(int v, bool morse, int* blocks_per_sm) {
-  const SysSet* none = nullptr;
-  (void)none;
   cudaError_t e = cudaErrorInvalidValue;
 #define QCAMS_OCC(M, B, N) \
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_integrate_persistent<M, B, N>, B, 0)
