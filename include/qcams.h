@@ -563,6 +563,20 @@ int qcams_debug_exp(const double* x, double* out_table, double* out_cuda, int64_
 int qcams_debug_force_math(const double* s, double alpha, double alpha_re, double* out_rinv,
                            double* out_arg, double* out_exp, int64_t n, void* cuda_stream);
 
+/*
+ * Diagnostic (test support): the integrator's float-float dot product, the
+ * arithmetic of its stage corrections and embedded error estimate (the
+ * Dormand-Prince step of Sec. 3.2): for n rows i,
+ *   out[i]   = sum_{q<m} w[q] a[i*m + q]  as a double (both operands split
+ *              into float pairs, compensated accumulation, rebuilt on the
+ *              integer pipe),
+ *   out_f[i] = the same sum rounded to FP32.
+ * a: device [n][m] row-major; w: device [m]; 1 <= m <= 8, else
+ * QCAMS_E_INVALID.  Device outputs of length n, caller-owned.  Asynchronous.
+ */
+int qcams_debug_ff_dot(const double* a, const double* w, int32_t m, double* out, float* out_f,
+                       int64_t n, void* cuda_stream);
+
 /* Device properties used for launch shapes: SM count and CC. */
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);
 

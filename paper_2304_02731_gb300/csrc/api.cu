@@ -1045,6 +1045,15 @@ int qcams_debug_force_math(const double* s, double alpha, double alpha_re, doubl
                                              (cudaStream_t)cuda_stream));
 }
 
+int qcams_debug_ff_dot(const double* a, const double* w, int32_t m, double* out, float* out_f,
+                       int64_t n, void* cuda_stream) {
+  if (n < 0 || m < 1 || m > 8 || (n > 0 && (!a || !w || !out || !out_f))) return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  if (n == 0) return QCAMS_OK;
+  return cuda_status(launch_ff_dot_check(a, w, m, out, out_f, n, (cudaStream_t)cuda_stream));
+}
+
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor) {
   if (!sm_count || !cc_major || !cc_minor) return QCAMS_E_INVALID;
   int dev = 0;

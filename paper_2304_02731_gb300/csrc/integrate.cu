@@ -632,6 +632,28 @@ __global__ void k_force_math_check(const double* s, double c0, double c1, float 
   e_out[i] = texp_hint(x, fmaf(-c0f, rf, c1f), sT);
 }
 
+// The integrator's float-float dot product on n rows of m <= 8 terms:
+// out[i] = sum_q w[q] a[i m + q] formed as in the stage corrections (both
+// operands split into float pairs, Dot2 accumulation, rebuilt as a double)
+// and out_f[i] = the same sum rounded to FP32 as the error estimate takes it.
+__global__ void k_ff_dot_check(const double* a, const double* w, int m, double* out,
+                               float* out_f, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.0f, c = 0.0f;
+  for (int q = 0; q < m; ++q) {
+    float wh, wl, ah, al;
+    split_ff(w[q], wh, wl);
+    split_ff(a[i * m + q], ah, al);
+    if (q == 0)
+      ff_dot_first(s, c, wh, wl, ah, al);
+    else
+      ff_dot_acc(s, c, wh, wl, ah, al);
+  }
+  out[i] = ff_to_double(s, c);
+  out_f[i] = s + c;
+}
+
 bool all_morse(const SysSet& s) {
   for (int k = 0; k < s.n; ++k)
     for (int p = 0; p < 3; ++p)
@@ -710,6 +732,12 @@ cudaError_t launch_force_math_check(const double* s, double c0, double c1, doubl
                                     double* x, double* e, long long n, cudaStream_t st) {
   k_force_math_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s, c0, c1, (float)c0,
                                                                   (float)c1, ri, x, e, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ff_dot_check(const double* a, const double* w, int m, double* out,
+                               float* out_f, long long n, cudaStream_t st) {
+  k_ff_dot_check<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, w, m, out, out_f, n);
   return cudaGetLastError();
 }
 

@@ -45,6 +45,10 @@ cudaError_t launch_exp_check(const double* x, double* mine, double* ref, long lo
 cudaError_t launch_force_math_check(const double* s, double c0, double c1, double* ri,
                                     double* x, double* e, long long n, cudaStream_t st);
 
+// Diagnostic: the integrator's float-float dot product (integrate.cu).
+cudaError_t launch_ff_dot_check(const double* a, const double* w, int m, double* out,
+                               float* out_f, long long n, cudaStream_t st);
+
 // Validation and launch helpers defined in api.cu.
 int prepare_run(const qcams_system* sys, int32_t n_sys, const qcams_integ* integ,
                 const qcams_batch* batch, SysSet* ss, IntegParams* ip, DevBatch* d);

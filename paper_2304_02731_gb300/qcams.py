@@ -36,7 +36,7 @@ GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
 EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
            "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
-           "qcams_debug_exp", "qcams_debug_force_math", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
+           "qcams_debug_exp", "qcams_debug_force_math", "qcams_debug_ff_dot", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
            "qcams_mlp_features", "qcams_mlp_fit_standardizer", "qcams_mlp_grad",
            "qcams_mlp_train_step", "qcams_mlp_train", "qcams_mlp_infer", "qcams_build_proposal",
            "qcams_sample_proposal", "qcams_rate_constants", "qcams_gb_distribution"]
@@ -143,6 +143,7 @@ def lib():
                 "qcams_run_batch_noalloc": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
                 "qcams_debug_exp": (C.c_int, [V, V, V, I64, V]),
                 "qcams_debug_force_math": (C.c_int, [V, D, D, V, V, V, I64, V]),
+                "qcams_debug_ff_dot": (C.c_int, [V, V, I32, V, V, I64, V]),
                 "qcams_autotune": (C.c_int, [P(System), I32, P(Integ), P(CBatch), I64,
                                              P(TuneResult), P(I32), P(Integ), V]),
                 "qcams_mlp_init": (C.c_int, [P(CMLP), C.c_uint64, V]),
@@ -444,6 +445,20 @@ def debug_force_math(s: torch.Tensor, alpha: float, alpha_re: float, stream=None
                                         ri.data_ptr(), x.data_ptr(), e.data_ptr(), s.numel(),
                                         _stream(stream)), "qcams_debug_force_math")
     return ri, x, e
+
+
+def debug_ff_dot(a: torch.Tensor, w: torch.Tensor, stream=None):
+    """qcams_debug_ff_dot: (sum_q w[q] a[:, q] as the integrator's float-float
+    dot product forms it, as a double and rounded to FP32) for device
+    tensors a [n, m] and w [m]."""
+    a = a.to(torch.float64).contiguous()
+    w = w.to(device=a.device, dtype=torch.float64).contiguous()
+    n, m = a.shape
+    out = torch.empty(n, dtype=torch.float64, device=a.device)
+    out_f = torch.empty(n, dtype=torch.float32, device=a.device)
+    _check(lib().qcams_debug_ff_dot(a.data_ptr(), w.data_ptr(), m, out.data_ptr(),
+                                    out_f.data_ptr(), n, _stream(stream)), "qcams_debug_ff_dot")
+    return out, out_f
 
 
 def debug_exp(x: torch.Tensor, stream=None):

@@ -492,6 +492,45 @@ def test_force_law_rsqrt_and_exp_accuracy(Q):
     assert torch.isnan(ri).all().item()
 
 
+def test_float_float_dot_matches_exact_sums(Q):
+    """The integrator's float-float dot product (its stage corrections and
+    embedded error estimate) against extended-precision sums: within
+    2^-43 sum|w a| + 2^-52 |sum| as a double (each operand split to 46 bits,
+    compensated accumulation: the split and the accumulation's second-order
+    term are both below 2^-44 sum|w a| for m <= 8, the reassembly truncates
+    below one double ulp), and within 2^-23 |sum| + 2^-40 sum|w a| in FP32.
+    Rows cover zero-sum weights on smooth data (the error estimate's heavy
+    cancellation), magnitudes over 20 decades, and m = 3..8.  Zero rows give
+    0, NaN gives NaN, values beyond 2^80 saturate to a finite sum."""
+    import torch
+    rng = np.random.default_rng(11)
+    n = 60_000
+    for m in (3, 4, 6, 8):
+        # zero-sum weights on a smooth sequence: cancellation like sum e_q a_q
+        w = rng.normal(size=m)
+        w[-1] = -w[:-1].sum()
+        hw = 10 ** rng.uniform(-3, -0.7, size=(n, 1))
+        ph = rng.uniform(0, 2 * np.pi, size=(n, 1))
+        amp = 10 ** rng.uniform(-6, 3, size=(n, 1))
+        smooth = amp * np.cos(ph + hw * np.arange(m) / m)
+        wide = rng.choice([-1.0, 1.0], size=(n, m)) * 10 ** rng.uniform(-10, 10, size=(n, m))
+        for a, ww in ((smooth, w), (wide, rng.normal(size=m) * 10 ** rng.uniform(-3, 3, size=m))):
+            out, out_f = (t.cpu().numpy() for t in Q.debug_ff_dot(torch.from_numpy(a).cuda(),
+                                                                   torch.from_numpy(ww)))
+            al, wl = a.astype(np.longdouble), ww.astype(np.longdouble)
+            ref = (al * wl).sum(axis=1)
+            sabs = np.abs(al * wl).sum(axis=1)
+            r = np.abs(out - ref) / (2.0 ** -43 * sabs + 2.0 ** -52 * np.abs(ref))
+            rf = np.abs(out_f.astype(np.longdouble) - ref) / (2.0 ** -23 * np.abs(ref) + 2.0 ** -40 * sabs)
+            print(f"\nm {m}: worst double error {float(r.max()):.3f}, FP32 {float(rf.max()):.3f} of the bounds")
+            assert float(r.max()) <= 1.0 and float(rf.max()) <= 1.0
+    special = torch.tensor([[0.0, 0.0, 0.0], [1.0, math.nan, 2.0], [1e30, -1e30, 5e29]],
+                           dtype=torch.float64, device="cuda")
+    out, out_f = Q.debug_ff_dot(special, torch.tensor([0.5, 0.25, 2.0], dtype=torch.float64))
+    out = out.cpu().numpy()
+    assert out[0] == 0.0 and np.isnan(out[1]) and np.isfinite(out[2])
+
+
 def test_autotune_restores_sample_and_shapes_agree(Q):
     """The autotuner leaves its sample untouched, and every launch shape
     integrates each lane identically (bit-for-bit)."""
