@@ -33,13 +33,13 @@ if ROOT not in sys.path:
 
 # FP64 floating-point operations per attempted integrator step of the Morse
 # kernel: 2 dfma + dmul + dadd, from ncu sass counters on the profile case
-# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 378 DFMA,
-# 155 DMUL, 19 DADD per lane-step, six right-hand sides included.  The FP64
-# pipe issues 378 + 155 + 19 = 552 instructions per step; the DFMA-chain
+# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 342 DFMA,
+# 137 DMUL, 37 DADD per lane-step, six right-hand sides included.  The FP64
+# pipe issues 342 + 137 + 37 = 516 instructions per step; the DFMA-chain
 # peak runs one DFMA (2 FLOP) per pipe slot, so pipe_frac below is the
 # fraction of the pipe's instruction rate the kernel uses.
-FP64_FLOP_PER_STEP = 930
-FP64_INSTR_PER_STEP = 552
+FP64_FLOP_PER_STEP = 858
+FP64_INSTR_PER_STEP = 516
 # FP32 floating-point operations per attempted step of the FP32 Morse kernel
 # (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
 # profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 392 FFMA,
@@ -50,13 +50,13 @@ FP64_INSTR_PER_STEP = 552
 FP32_FLOP_PER_STEP = 1049
 FP32_THREAD_INSTR_PER_STEP = 946
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the FP64 profile case (1,043,200 B read, nothing
+# dram__bytes_write.sum of the FP64 profile case (1,219,840 B read, nothing
 # written back during the launch, for 3,840 lanes), per lane: the state is
 # loaded once, everything else is in registers; the 16 KB exponential table
 # is read from DRAM once and served from L2 to the other blocks.  The figure
 # also holds the fetch of the kernel's code (it moved with the code size
 # between kernel versions: 0.68-1.2 MB), a fixed cost per launch.
-DRAM_BYTES_PER_LANE = 1043200 / 3840
+DRAM_BYTES_PER_LANE = 1219840 / 3840
 # The same for the FP32 kernel (560,896 B read, no table): its state is
 # loaded as (value, compensation) pairs from the same FP64 arrays.
 DRAM_BYTES_PER_LANE_FP32 = 560896 / 3840

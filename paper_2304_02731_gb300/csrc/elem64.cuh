@@ -4,11 +4,12 @@
 // 128 FP32 lanes), so each routine takes an FP32 estimate and finishes it
 // with as few FP64 instructions as its accuracy needs:
 //   rsqrt_seeded   1/sqrt(s) in 3 FP64 instructions (plus an FP32 sqrt(s)),
-//   texp_hint      e^x in 5, given an FP32 approximation of x.
+//   texp_hint      e^x in 3, given an FP32 approximation of x.
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include "ff.cuh"
 #include "texp.cuh"
 
 namespace qcams {
@@ -66,8 +67,13 @@ constexpr float kExpInvLf = (float)kExpInvL;
 // x = -700 it grows to about 2e-14 relative, on values below 1e-304.  The
 // reduction uses ln2/N rounded to a double, without the tail constant: that
 // adds an error of |x| 2^-54.7 to the argument, below the |x| 2^-53 that the
-// rounding of x itself already carries.  FP64 work: the reduction, three
-// for the cubic, one for the table product.
+// rounding of x itself already carries.
+// With |r| <= 2.1e-4, e^r - 1 = r + w, w = r^2/2 + r^3/6 <= 2.2e-8: w is
+// needed to ~1e-18 absolute (the result's relative error is that of 1 + r +
+// w), so r^2/2 is formed in float-float (r split into a float pair on the
+// integer pipe, r_h^2 split exactly by an FMA) and r^3/6 <= 1.5e-12 in
+// FP32, then w is rebuilt as a double on the integer pipe.  FP64 work: the
+// reduction, r + w, and the table product.
 __device__ __forceinline__ double texp_hint(double x, float xa, const double* __restrict__ T) {
   const float kf = fmaf(xa, kExpInvLf, 12582912.0f);   // 1.5 * 2^23 + k
   const int k = __float_as_int(kf) - 0x4B400000;
@@ -75,9 +81,12 @@ __device__ __forceinline__ double texp_hint(double x, float xa, const double* __
   const unsigned khi = (kb & 0x80000000u) | (((kb & 0x7fffffffu) >> 3) + (896u << 20));
   const double kd = __hiloint2double(kb ? (int)khi : 0, (int)(kb << 29));
   const double r = fma(-kd, kExpL1, x);
-  double q = fma(r, 1.0 / 6.0, 0.5);
-  q = q * r;
-  const double p = fma(q, r, r);
+  float rh, rl;
+  split_ff(r, rh, rl);
+  const float P = __fmul_rn(rh, rh);
+  const float Pl = fmaf(2.0f * rh, rl, fmaf(rh, rh, -P));   // r^2 = P + Pl to 2^-46
+  const float cub = (P * rh) * (1.0f / 6.0f);
+  const double p = r + ff_to_double(0.5f * P, fmaf(0.5f, Pl, cub));
   const double Tj = T[k & (kExpTableSize - 1)];
   const double y = fma(Tj, p, Tj);
   const double ex = __hiloint2double(__double2hiint(y) + ((k >> 11) << 20), __double2loint(y));
