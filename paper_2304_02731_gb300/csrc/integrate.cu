@@ -26,10 +26,11 @@
 //    controller's error norm (magnitudes taken from the doubles' exponent and
 //    leading mantissa bits, ratios in FP32), the stop tests (integer compares
 //    of non-negative doubles) and the minimum-step test (exponent compare).
-//  * Each pair force takes 1/sqrt(s) and e^x (elem64.cuh): an FP32 hardware
-//    estimate finished in FP64, 3 FP64 instructions for the reciprocal
-//    square root and 5 for the exponential (Tang's table method, a 2048-entry
-//    table of 2^(j/2048) in shared memory, the table index rounded in FP32).
+//  * Each pair force takes 1/sqrt(s) and e^x (elem64.cuh), 3 FP64
+//    instructions each: the reciprocal square root is an FP32 hardware
+//    estimate finished in FP64; the exponential is Tang's table method (a
+//    2048-entry table of 2^(j/2048) in shared memory, the table index
+//    rounded in FP32, the quadratic and cubic terms in float-float).
 //  * Stages 6 and 7 (c = 1) share rho + h v, and the tableau entries that are
 //    zero in exact arithmetic are skipped at compile time.
 //  * Linear combinations that do not need an FP64 result run as float-float
