@@ -66,6 +66,8 @@ def test_system_setup_matches_oracle(Q, oracle):
     dict(mass_u=(1.0, 1.0, 40.0), pairs=(("lj", 12.5, 6, 1.0, 1.0, 3.0),) * 3),
     dict(mass_u=(1.0, 1.0, 40.0), pairs=(("lj", 12, 2, 1.0, 1.0, 3.0),) * 3),
     dict(mass_u=(1.0, float("nan"), 40.0), pairs=(("morse", 0.17, 1.4, 1.0),) * 3),
+    # alpha re >= 700: e^{alpha (re - r)} would overflow near r = 0
+    dict(mass_u=(1.0, 1.0, 40.0), pairs=(("morse", 0.17, 1.4, 600.0),) * 3),
 ])
 def test_system_setup_rejects_bad_parameters(Q, bad):
     with pytest.raises(Q.QcamsError) as e:
@@ -106,6 +108,14 @@ def test_entry_points_reject_bad_arguments_without_a_device(Q):
     assert L.qcams_last_run_stats(None, None) == -1
     f = C.c_double()
     assert L.qcams_fma_peak(16, C.byref(f), None) == -1
+    # diagnostics: sizes and the Morse argument range are checked first
+    p8 = C.c_void_p(8)
+    assert L.qcams_debug_force_math(None, 1.0, 1.4, None, None, None, -1, None) == -1
+    assert L.qcams_debug_force_math(p8, 1.0, 700.0, p8, p8, p8, 1, None) == -1
+    assert L.qcams_debug_force_math(p8, -1.0, 1.4, p8, p8, p8, 1, None) == -1
+    assert L.qcams_debug_ff_dot(p8, p8, 0, p8, p8, 1, None) == -1
+    assert L.qcams_debug_ff_dot(p8, p8, 9, p8, p8, 1, None) == -1
+    assert L.qcams_debug_ff_dot(None, p8, 3, p8, p8, 1, None) == -1
 
 
 def test_rate_constants_match_oracle(Q, oracle):
