@@ -434,6 +434,12 @@ def run_ours(args):
                    + f", block {integ.block or 128} x {integ.blocks_per_sm or 1}/SM variant",
                    "autotune": tune,
                    "rtol": wl.integ["rtol"], "atol": wl.integ["atol"],
+                   "arithmetic": ("FP64 state, forces and new-state sums; stage corrections, "
+                                  "the error estimate and the exponential's quadratic as "
+                                  "float-float (FP32 pairs); error norm in FP32"
+                                  if args.precision == 64 else
+                                  "FP32 stages with compensated (Kahan) state updates; "
+                                  "FP64 time, levels and product analysis"),
                    "l2": "inputs larger than L2 (SoA state > 129 MB)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
