@@ -329,6 +329,27 @@ def test_dopri5_order_conditions(oracle):
     assert A[6][:6] == b[:6] and b[6] == 0 and c[6] == 1
 
 
+def test_dopri5_rkn_products_zero_exactly_where_the_integrators_skip(oracle):
+    """The CUDA integrators use the Runge-Kutta-Nystrom products (A^2)_{sq}
+    for the stage positions and (e^T A)_q for the position error (Sec. 3.2's
+    Dormand-Prince step written for rho'' = a) and skip the terms they take
+    to be zero: (A^2)_{sq} for q >= s - 1 and for (s, q) = (7, 2), (e^T A)_q
+    for q = 2 and 7.  In exact arithmetic on the tableau those are zero,
+    (A^2)_{7q} = b_q (1 - c_q), and every other product is nonzero, so the
+    skipped set is exactly the zero set."""
+    c, A, b, bs = _tableau_exact(oracle)
+    e = [b[i] - bs[i] for i in range(7)]
+    A2 = [[sum(A[s][j] * A[j][q] for j in range(7)) for q in range(7)] for s in range(7)]
+    eA = [sum(e[i] * A[i][q] for i in range(7)) for q in range(7)]
+    for s in range(1, 7):            # 0-based stage s + 1 = 2..7
+        for q in range(s):           # 0-based q + 1 = 1..s
+            skipped = q >= s - 1 or (s, q) == (6, 1)
+            assert (A2[s][q] == 0) == skipped, (s + 1, q + 1, A2[s][q])
+    for q in range(7):
+        assert A2[6][q] == b[q] * (1 - c[q])
+        assert (eA[q] == 0) == (q in (1, 6)), (q + 1, eA[q])
+
+
 def test_dopri5_stability_polynomial(oracle):
     """One step on y' = lambda y multiplies y by R(z) = 1 + sum b^T A^(k-1) 1 z^k;
     for Dormand-Prince 5(4) the z^6 coefficient is 1/600."""
