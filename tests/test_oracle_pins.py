@@ -716,3 +716,220 @@ def test_adaptive_controller_matches_scipy_rk45(oracle):
         dy = np.max(np.abs(yi - y[0]) / (np.abs(y[0]) + 1.0))
         print(f"\nrtol {rtol:g}: {n} accepted steps both; |dt|/t {dt:.1e}, state {dy:.1e}")
         assert dt < 1e-7 and dy < 100 * rtol
+
+
+# ---------------------------------------------------------------------------
+# Stop rules (Sec. 3.1: r_stop, the largest distance between any two atoms;
+# t_stop, a multiple of the trajectory's time scale d / v_c) and the
+# Buckingham collapse (Sec. 3.2 item 3, the short-range "max").
+#
+# Each rule is checked against an independent integration: scipy's RK45
+# (pinned to the oracle's controller above) stepped on Hamilton's equations,
+# with the rule evaluated after every accepted step on CARTESIAN atom
+# positions and velocities, as the paper states it.  The oracle must stop on
+# exactly the same accepted step.  Plausible misreadings (no outward-motion
+# condition, the atom-molecule distance instead of the largest pair distance,
+# the wrong pair, the well instead of the barrier) are shown to stop on other
+# steps, so each would fail.
+# ---------------------------------------------------------------------------
+def _T_REL(rtol):
+    """Stop times of two valid RK45 implementations agree to about
+    50 eps / rtol relative: the embedded error estimate is a cancellation
+    whose rounding is ~eps / rtol of the norm, and the step sizes inherit
+    it (the controller pin above shows the same)."""
+    return 50 * 2.220446049250313e-16 / rtol
+
+
+def _cartesian_view(oracle, s, y):
+    m = np.array([s.m[0], s.m[1], s.m[2]])
+    x = oracle.jacobi_to_cartesian(s, y)
+    return x[:9].reshape(3, 3), x[9:].reshape(3, 3) / m[:, None], m
+
+
+def _pair_distances(pos):
+    return [float(np.linalg.norm(pos[i] - pos[k])) for i, k in ((0, 1), (1, 2), (2, 0))]
+
+
+def _atom_leaving(pos, vel, m):
+    """Atom C moves away from the centre of mass of A and B."""
+    cm = (m[0] * pos[0] + m[1] * pos[1]) / (m[0] + m[1])
+    vcm = (m[0] * vel[0] + m[1] * vel[1]) / (m[0] + m[1])
+    return float(np.dot(pos[2] - cm, vel[2] - vcm)) > 0.0, float(np.linalg.norm(pos[2] - cm))
+
+
+def _scipy_first_step(oracle, s, y0, rtol, atol, rule, t_end, max_steps=100_000):
+    """First accepted scipy RK45 step (1-based index, time) whose end state
+    satisfies rule(pos, vel, m); None if none before t_end."""
+    from scipy.integrate import RK45
+    solver = RK45(lambda t, x: oracle.rhs(s, x), 0.0, np.asarray(y0, float), t_bound=1e12,
+                  rtol=rtol, atol=atol)
+    n = 0
+    while solver.t < t_end and n < max_steps:
+        solver.step()
+        assert solver.status == "running"
+        n += 1
+        pos, vel, m = _cartesian_view(oracle, s, solver.y)
+        if rule(pos, vel, m):
+            return n, solver.t
+    return None
+
+
+def _oracle_run_from(oracle, s, y0, integ, t_scale=1.0):
+    y = np.asarray(y0, float)[None].copy()
+    E0 = np.array([oracle.hamiltonian(s, y[0])])
+    res = oracle.run_adaptive([s], np.zeros(1, np.int32), integ, y, np.array([t_scale]), E0,
+                              np.zeros(1, np.int32))
+    return res[0], y[0]
+
+
+def test_stop_rule_against_scipy_and_cartesian_definition(oracle):
+    """r_stop (Sec. 3.1): the trajectory ends after the first accepted step at
+    which the largest distance between any two atoms exceeds r_stop while the
+    atom leaves the molecule.  Lanes start at R0 = 40 > r_stop = 35 moving in
+    (the outward condition keeps them running through the collision); the
+    same states with all momenta reversed move out and stop after one step.
+    The time scale t_scale of Sec. 3.1 (t_max = t_stop d / v_c) is the
+    initial atom-molecule distance over the initial relative speed."""
+    s = oracle.system_from_spec(W.SYS_H2_CA_MORSE)
+    rtol, atol, r_stop = 1e-8, 1e-10, 35.0
+    integ = oracle.make_integ(rtol=rtol, atol=atol, r_stop=r_stop, t_stop=100.0)
+    E = np.array([0.10, 0.10, 0.10])
+    b = np.array([0.0, 3.0, 6.0])
+    v = np.array([0, 0, 1], np.int32)
+    j = np.array([0, 3, 2], np.int32)
+    st = oracle.init([s], np.zeros(3, np.int32), E, b, v, j, 40.0, 5)
+    mu123 = oracle.reduced_masses(s)["mu123"]
+
+    def rule_max(pos, vel, m):
+        return max(_pair_distances(pos)) > r_stop and _atom_leaving(pos, vel, m)[0]
+
+    def rule_no_outward(pos, vel, m):
+        return max(_pair_distances(pos)) > r_stop
+
+    def rule_R(pos, vel, m):
+        out, R = _atom_leaving(pos, vel, m)
+        return R > r_stop and out
+
+    differs_R = 0
+    for i in range(3):
+        y0 = st["y"][i].copy()
+        pos, vel, m = _cartesian_view(oracle, s, y0)
+        leaving, R = _atom_leaving(pos, vel, m)
+        assert not leaving and max(_pair_distances(pos)) > r_stop
+        speed = float(np.linalg.norm(vel[2] - (m[0] * vel[0] + m[1] * vel[1]) / (m[0] + m[1])))
+        assert speed == pytest.approx(math.sqrt(2 * E[i] / mu123), rel=1e-12)
+        assert st["t_scale"][i] == pytest.approx(R / speed, rel=1e-12)
+        r, _ = _oracle_run_from(oracle, s, y0, integ, st["t_scale"][i])
+        t_end = 100.0 * st["t_scale"][i]
+        ref = _scipy_first_step(oracle, s, y0, rtol, atol, rule_max, t_end)
+        assert ref is not None
+        print(f"\nlane {i}: oracle status {r['status']} after {r['nsteps']} accepted steps "
+              f"(t = {r['t']:.6f}); scipy + Cartesian rule: step {ref[0]} (t = {ref[1]:.6f})")
+        assert r["status"] == 2 and r["nsteps"] == ref[0]
+        assert r["t"] == pytest.approx(ref[1], rel=_T_REL(rtol))
+        # the misreadings stop elsewhere
+        assert _scipy_first_step(oracle, s, y0, rtol, atol, rule_no_outward, t_end)[0] == 1
+        alt = _scipy_first_step(oracle, s, y0, rtol, atol, rule_R, t_end)
+        differs_R += alt[0] != ref[0]
+        # reversed momenta: the atom leaves from the start, one step
+        yr = y0.copy()
+        yr[6:12] *= -1.0
+        r, _ = _oracle_run_from(oracle, s, yr, integ, st["t_scale"][i])
+        assert r["status"] == 2 and r["nsteps"] == 1
+        assert _scipy_first_step(oracle, s, yr, rtol, atol, rule_max, t_end)[0] == 1
+    assert differs_R >= 2
+
+
+def _buck_barrier():
+    """Inner barrier of the Buckingham Ca-H pair, V = A e^{-B r} - C6 / r^6
+    (Sec. 3.2 item 3): the root of V'(r) below the well, by brentq."""
+    from scipy.optimize import brentq
+    A, B, C6 = W.CAH_BUCK[1:4]
+    dV = lambda r: -A * B * math.exp(-B * r) + 6.0 * C6 / r ** 7
+    return brentq(dV, 1.0, 3.5, xtol=1e-15)
+
+
+def _collapse_states(oracle, s, side, speeds, gap=2.3, re=1.40):
+    """Molecule AB on the x axis (rigid, both atoms at velocity u toward atom
+    C, at rest): side "A" puts C at distance `gap` beyond A, side "B" beyond
+    B.  Returns Jacobi states."""
+    m = np.array([s.m[0], s.m[1], s.m[2]])
+    out = []
+    for u in speeds:
+        if side == "A":
+            xA, xB, xC, vv = [0, 0, 0], [-re, 0, 0], [gap, 0, 0], [u, 0, 0]
+        else:
+            xA, xB, xC, vv = [re, 0, 0], [0, 0, 0], [-gap, 0, 0], [-u, 0, 0]
+        x = np.concatenate([xA, xB, xC, m[0] * np.array(vv), m[1] * np.array(vv),
+                            np.zeros(3)]).astype(float)
+        out.append(oracle.cartesian_to_jacobi(s, x))
+    return out
+
+
+def test_buckingham_collapse_rule_against_scipy(oracle):
+    """A Buckingham pair that falls inside its short-range maximum r_b
+    (Sec. 3.2 item 3, the 'max' where the potential turns over and
+    collapses) ends the lane with FAIL_COLLAPSE after the first accepted step
+    at which its distance is below r_b.  r_b comes from brentq on V' of the
+    paper's formula; the step from scipy's RK45 with the distance test on
+    Cartesian positions.  Fast approaches of atom C toward A (pair CA) and
+    toward B (pair BC) collapse; a slower one turns around 0.09 bohr outside
+    r_b and runs to r_stop; a pair started inside r_b collapses on the first
+    step; the same approaches in a system whose BC pair is Morse collapse
+    only on the CA side."""
+    rb = _buck_barrier()
+    rtol, atol = 1e-10, 1e-12
+    integ = oracle.make_integ(rtol=rtol, atol=atol, r_stop=35.0, t_stop=3000.0)
+    s = oracle.system_from_spec(W.SYS_H2_CA_BUCK)
+    mu = oracle.reduced_masses(s)
+    assert oracle.stationary(s.pair[2], mu["mu_CA"], 0.0)["r_inner"] == pytest.approx(rb, rel=1e-9)
+    one_sided = dict(mass_u=W.MASS_H2_CA, pairs=(W.HH_MORSE, W.CAH_MORSE, W.CAH_BUCK))
+    s1 = oracle.system_from_spec(one_sided)
+
+    def collapse_in(kinds):
+        def rule(pos, vel, m):
+            d = _pair_distances(pos)
+            return any(d[k] < rb for k in kinds)
+        return rule
+
+    def closest(sys_, y0, t_end):
+        from scipy.integrate import RK45
+        solver = RK45(lambda t, x: oracle.rhs(sys_, x), 0.0, y0, t_bound=1e12, rtol=rtol,
+                      atol=atol)
+        dmin = [math.inf] * 3
+        while solver.t < t_end:
+            solver.step()
+            d = _pair_distances(_cartesian_view(oracle, sys_, solver.y)[0])
+            dmin = [min(a, c) for a, c in zip(dmin, d)]
+            if max(d) > 35.0:
+                break
+        return dmin
+
+    cases = []   # (system, state, Buckingham pair indices, expect collapse)
+    for side, pair in (("A", 2), ("B", 1)):
+        for y0 in _collapse_states(oracle, s, side, [0.008, 0.02, 0.047]):
+            cases.append((s, y0, (1, 2), True))
+        cases.append((s, _collapse_states(oracle, s, side, [0.006])[0], (1, 2), False))
+        cases.append((s, _collapse_states(oracle, s, side, [0.0], gap=2.0)[0], (1, 2), True))
+    cases.append((s1, _collapse_states(oracle, s1, "A", [0.02])[0], (2,), True))
+    cases.append((s1, _collapse_states(oracle, s1, "B", [0.02])[0], (2,), False))
+    for sys_, y0, kinds, expect in cases:
+        r, _ = _oracle_run_from(oracle, sys_, y0, integ)
+        ref = _scipy_first_step(oracle, sys_, y0, rtol, atol, collapse_in(kinds), 3000.0)
+        if expect:
+            assert ref is not None
+            assert r["status"] == 7 and r["cls"] == 5 and r["nsteps"] == ref[0], (r, ref)
+            assert r["t"] == pytest.approx(ref[1], rel=_T_REL(rtol))
+        else:
+            assert ref is None
+            assert r["status"] == 2, r
+    # the turning point of the slow approach lies outside r_b but inside
+    # the Buckingham well's minimum (a test against the well would fire)
+    dmin = closest(s, _collapse_states(oracle, s, "A", [0.006])[0], 3000.0)
+    r_well = oracle.stationary(s.pair[2], mu["mu_CA"], 0.0)["r_min"]
+    print(f"\nr_b = {rb:.10f} bohr; slow approach turns at {dmin[2]:.4f} bohr; well at {r_well:.3f}")
+    assert rb < dmin[2] < rb + 0.15 and dmin[2] < r_well
+    # the Morse BC pair of the one-sided system passes inside r_b unharmed
+    # while its Buckingham CA pair stays outside
+    dmin = closest(s1, _collapse_states(oracle, s1, "B", [0.02])[0], 3000.0)
+    assert dmin[1] < rb < dmin[2]
