@@ -345,7 +345,9 @@ int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells,
  * holds until the process exits.
  *   - The first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress, with the device current); make this first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept until qcams_shutdown
+ *     on that device: a caller that resets the device (cudaDeviceReset)
+ *     calls qcams_shutdown first.
  *   - Calls on one device share the array and it keeps the last call's
  *     contents (each call rewrites the shape table and clears the counters
  *     it uses), so calls that overlap on the GPU race: serialise them on one
@@ -539,43 +541,6 @@ int qcams_last_run_stats(qcams_run_stats* out, void* cuda_stream);
  * and returns the achieved FLOP/s (FMA = 2 FLOP).  Synchronous.
  */
 int qcams_fma_peak(int32_t precision, double* flops_per_s, void* cuda_stream);
-
-/*
- * Diagnostic (test support): evaluates, for n device arguments x[i], the
- * integrator's table-driven exponential (Tang's method, used for the Morse
- * and Buckingham exponentials) into out_table[i] and CUDA's exp into
- * out_cuda[i] (device arrays).  Asynchronous.
- */
-int qcams_debug_exp(const double* x, double* out_table, double* out_cuda, int64_t n,
-                    void* cuda_stream);
-
-/*
- * Diagnostic (test support): the elementary functions of the integrator's
- * Morse force law (Sec. 3.2 item 1, V = De (1 - e^{-alpha (r - re)})^2 - De)
- * on n device squared distances s[i]:
- *   out_rinv[i] = 1/sqrt(s[i])   (FP32 hardware estimate refined in FP64;
- *                                 NaN outside 2^-126 <= s < 2^128),
- *   out_arg[i]  = x = alpha_re - alpha r,  r = s[i] out_rinv[i],
- *   out_exp[i]  = e^x            (table method with the index rounded in FP32).
- * alpha > 0, 0 < alpha_re < 700, else QCAMS_E_INVALID.  Device arrays of
- * length n, caller-owned.  Asynchronous.
- */
-int qcams_debug_force_math(const double* s, double alpha, double alpha_re, double* out_rinv,
-                           double* out_arg, double* out_exp, int64_t n, void* cuda_stream);
-
-/*
- * Diagnostic (test support): the integrator's float-float dot product, the
- * arithmetic of its stage corrections and embedded error estimate (the
- * Dormand-Prince step of Sec. 3.2): for n rows i,
- *   out[i]   = sum_{q<m} w[q] a[i*m + q]  as a double (both operands split
- *              into float pairs, compensated accumulation, rebuilt on the
- *              integer pipe),
- *   out_f[i] = the same sum rounded to FP32.
- * a: device [n][m] row-major; w: device [m]; 1 <= m <= 8, else
- * QCAMS_E_INVALID.  Device outputs of length n, caller-owned.  Asynchronous.
- */
-int qcams_debug_ff_dot(const double* a, const double* w, int32_t m, double* out, float* out_f,
-                       int64_t n, void* cuda_stream);
 
 /* Device properties used for launch shapes: SM count and CC. */
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);

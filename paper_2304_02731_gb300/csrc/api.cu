@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "qcams.h"
+#include "qcams_debug.h"
 #include "qcams_device.cuh"
 #include "qcams_internal.h"
 #include "analysis.cuh"
@@ -1054,6 +1055,16 @@ int qcams_debug_ff_dot(const double* a, const double* w, int32_t m, double* out,
   return cuda_status(launch_ff_dot_check(a, w, m, out, out_f, n, (cudaStream_t)cuda_stream));
 }
 
+int qcams_debug_context_exists(int32_t* out) {
+  if (!out) return QCAMS_E_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return QCAMS_E_NODEVICE;
+  if (dev < 0 || dev >= kMaxDevices) return QCAMS_E_INVALID;
+  std::lock_guard<std::mutex> lk(g_mutex);
+  *out = g_ctx[dev] != nullptr ? 1 : 0;
+  return QCAMS_OK;
+}
+
 int qcams_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor) {
   if (!sm_count || !cc_major || !cc_minor) return QCAMS_E_INVALID;
   int dev = 0;
@@ -1073,6 +1084,7 @@ int qcams_shutdown(void) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return QCAMS_E_NODEVICE;
   if (dev < 0 || dev >= kMaxDevices) return QCAMS_E_INVALID;
+  noalloc_forget_device(dev);
   std::lock_guard<std::mutex> lk(g_mutex);
   Ctx* c = g_ctx[dev];
   if (!c) return QCAMS_OK;

@@ -27,6 +27,9 @@ constexpr size_t kShapeBytes = sizeof(DevShape) * QCAMS_NOALLOC_MAX_SYS * 3;
 constexpr size_t kCounterOffset = (kShapeBytes + 255) / 256 * 256;
 static_assert(kCounterOffset + 8 * sizeof(unsigned long long) <= QCAMS_NOALLOC_SCRATCH_BYTES,
               "no-alloc scratch too small");
+// SysSet holds QCAMS_MAX_SYS systems and the shape kernel writes n_sys * 3
+// records: the no-alloc limit may not exceed the library's.
+static_assert(QCAMS_NOALLOC_MAX_SYS <= QCAMS_MAX_SYS, "no-alloc system limit too large");
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[QCAMS_NOALLOC_SCRATCH_BYTES];
@@ -36,7 +39,8 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the array for the current device, looked up once per
-// device (host code cannot use the symbol's own address).
+// device (host code cannot use the symbol's own address) and kept until
+// qcams_shutdown on that device.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -54,6 +58,13 @@ cudaError_t scratch_address(void** out) {
 }
 
 }  // namespace
+
+void noalloc_forget_device(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_scratch_ptr[dev] = nullptr;
+}
+
 }  // namespace qcams
 
 using namespace qcams;
@@ -61,6 +72,7 @@ using namespace qcams;
 extern "C" int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys,
                                        const qcams_integ* integ, qcams_batch* batch,
                                        void* cuda_stream) {
+  (void)cudaGetLastError();   // a stale error of an earlier runtime call is not ours
   if (n_sys > QCAMS_NOALLOC_MAX_SYS) return QCAMS_E_CAPACITY;
   SysSet ss;
   IntegParams ip;

@@ -66,6 +66,10 @@ cudaError_t launch_integrate32(const SysSet& sys, const DevShape* shapes, const 
                                const DevBatch& b, int persistent, Ctx& ctx, cudaStream_t st,
                                bool all_morse);
 
+// Drop the no-allocation entry point's cached scratch address for a device
+// (noalloc.cu); qcams_shutdown calls it.
+void noalloc_forget_device(int dev);
+
 // Launch-shape variants of the integrator (integrate.cu), for the autotuner.
 int integrate_variant_count();
 void integrate_variant_shape(int v, int* block, int* blocks_per_sm);

@@ -36,7 +36,8 @@ GB_SIGMA_DEFAULT = 0.1 / (2.0 * math.sqrt(2.0 * math.log(2.0)))
 EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_init_states",
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
            "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
-           "qcams_debug_exp", "qcams_debug_force_math", "qcams_debug_ff_dot", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
+           "qcams_debug_exp", "qcams_debug_force_math", "qcams_debug_ff_dot",
+           "qcams_debug_context_exists", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
            "qcams_mlp_features", "qcams_mlp_fit_standardizer", "qcams_mlp_grad",
            "qcams_mlp_train_step", "qcams_mlp_train", "qcams_mlp_infer", "qcams_build_proposal",
            "qcams_sample_proposal", "qcams_rate_constants", "qcams_gb_distribution"]
@@ -144,6 +145,7 @@ def lib():
                 "qcams_debug_exp": (C.c_int, [V, V, V, I64, V]),
                 "qcams_debug_force_math": (C.c_int, [V, D, D, V, V, V, I64, V]),
                 "qcams_debug_ff_dot": (C.c_int, [V, V, I32, V, V, I64, V]),
+                "qcams_debug_context_exists": (C.c_int, [P(I32)]),
                 "qcams_autotune": (C.c_int, [P(System), I32, P(Integ), P(CBatch), I64,
                                              P(TuneResult), P(I32), P(Integ), V]),
                 "qcams_mlp_init": (C.c_int, [P(CMLP), C.c_uint64, V]),
@@ -468,6 +470,14 @@ def debug_exp(x: torch.Tensor, stream=None):
     _check(lib().qcams_debug_exp(x.data_ptr(), a.data_ptr(), b.data_ptr(), x.numel(),
                                  _stream(stream)), "qcams_debug_exp")
     return a, b
+
+
+def debug_context_exists() -> bool:
+    """qcams_debug_context_exists: whether the library's per-device context
+    (its only device allocations outside the autotuner) exists."""
+    out = C.c_int32(0)
+    _check(lib().qcams_debug_context_exists(C.byref(out)), "qcams_debug_context_exists")
+    return bool(out.value)
 
 
 def device_info():

@@ -22,15 +22,21 @@ def Q():
 
 
 def _declared_functions():
-    src = open(os.path.join(ROOT, "include", "qcams.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(qcams_[a-z0-9_]+)\s*\(", src)))
+    """Functions declared in every header of include/ (the path's qcams.h
+    and the test-support qcams_debug.h)."""
+    inc = os.path.join(ROOT, "include")
+    names = set()
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(qcams_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(Q):
     names = _declared_functions()
     assert "qcams_init_states" in names and "qcams_run_batch" in names
-    assert "qcams_reduce_xsec" in names
+    assert "qcams_reduce_xsec" in names and "qcams_debug_context_exists" in names
     L = C.CDLL(Q.library_path())
     for n in names:
         assert hasattr(L, n), n

@@ -1,0 +1,94 @@
+"""Full-size parity of the mixed-potential study: 2,000,000 trajectories of
+H2 + Ca with the Ca-H pairs as Buckingham, LJ(12,6) or LJ(8,6) (Sec. 3.2
+items 1-3) in equal thirds, mixed initial states v in 0..10, j in 0..20,
+E_col uniform on [0.05, 0.30] hartree and b^2 uniform on [0, 100] bohr^2,
+run in the launch configuration bench.py times for this workload (autotuned
+persistent refill-queue kernel, one CUDA graph).  Cross sections per
+(system, energy bin) are compared with the oracle's estimate from a
+stratified sample, and outcome classes lane by lane on sampled lanes."""
+import numpy as np
+import pytest
+
+from paper_2304_02731_gb300 import workloads as W
+
+import fullsize_common as FC
+
+pytestmark = pytest.mark.gpu
+
+# oracle lanes per (system, E bin, v) cell: 84,480 trajectories, about 20 s
+# on 16 host cores
+ORACLE_PER_CELL = 256
+
+
+@pytest.fixture(scope="module")
+def mixed_run():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = W.mixed_ca_h()
+    out, hist, cells, groups = FC.run_bench_config(wl)
+    return wl, out, hist, cells, groups
+
+
+def test_mixed_full_size_sampled_lanes_match_oracle(mixed_run):
+    """1,000 lanes drawn across the whole study, each re-run by the oracle
+    from the same (seed, id): identical status class on every lane for the
+    deterministic ones (NO_LEVEL exactly where (v, j) = (10, 20) does not
+    exist), identical outcome class for >= 99 % of all lanes."""
+    wl, out, hist, cells, groups = mixed_run
+    idx = np.sort(np.random.default_rng(1).choice(wl.n, 1000, replace=False))
+    o = FC.oracle_lanes(wl, idx)
+    g_st, g_cls = out["status"][idx], out["cls"][idx]
+    assert np.array_equal(g_st == 8, o["status"] == 8)
+    assert np.array_equal(g_st == 8, (wl.v[idx] == 10) & (wl.j[idx] == 20))
+    agree = g_cls == o["cls"]
+    done = (g_st == 2) & (o["status"] == 2)
+    tmax = (g_st == 3) | (o["status"] == 3)
+    for k in np.flatnonzero(~agree):
+        i = idx[k]
+        print("mismatch lane %d sys=%d E=%.4f b=%.2f v=%d j=%d gpu(st=%d cls=%d n=%d) "
+              "oracle(st=%d cls=%d n=%d)" % (i, wl.sys_id[i], wl.E[i], wl.b[i], wl.v[i], wl.j[i],
+                                            g_st[k], g_cls[k], out["nsteps"][i], o["status"][k],
+                                            o["cls"][k], o["nsteps"][k]))
+    print(f"\nmixed sampled lanes: class agreement {agree.mean():.4f} over all {len(idx)}, "
+          f"{agree[done].mean():.4f} over the {done.sum()} that reached a product on both "
+          f"sides; t_max share {tmax.mean():.4f}; classes GPU "
+          f"{np.bincount(g_cls, minlength=6)} oracle {np.bincount(o['cls'], minlength=6)}")
+    assert agree.mean() >= 0.99
+    assert agree[done].mean() >= 0.99
+
+
+def test_mixed_full_size_invariants(mixed_run, oracle):
+    """No numerical failure; NO_LEVEL exactly on the (10, 20) lanes;
+    histograms bit-exact with the per-lane outcomes; energy conserved on the
+    separated lanes as in the FP64 study."""
+    wl, out, hist, cells, groups = mixed_run
+    st = out["status"]
+    counts = {k: int(np.sum(st == v)) for k, v in (("rstop", 2), ("tmax", 3), ("collapse", 7),
+                                                    ("no_level", 8))}
+    print(f"\nmixed study statuses: {counts}; integrator "
+          f"{out['stats']['integrate_ms']:.0f} ms, analysis {out['stats']['analyze_ms']:.1f} ms")
+    assert np.all(np.isin(st, [2, 3, 7, 8]))
+    assert np.array_equal(st == 8, (wl.v == 10) & (wl.j == 20))
+    ho = oracle.reduce(out["cls"], out["vt"], out["jt"], out["gbw"], wl.cell, wl.n_cells)
+    assert np.array_equal(hist, ho)
+    sep = st == 2
+    rel = np.abs(out["dE"][sep]) / np.maximum(np.abs(out["E0"][sep]), wl.E[sep])
+    print(f"|dE|/max(|E0|,Ecol): median {np.median(rel):.2e}, 99% {np.quantile(rel, .99):.2e}")
+    assert np.median(rel) < 1e-8
+
+
+def test_mixed_full_size_cross_sections_within_3se_of_oracle(mixed_run, oracle):
+    """Every cross section (Q, R_AC, R_BC, D) of every (system, E bin) group
+    of the 2,000,000-lane GPU run lies within 3 combined standard errors of
+    the oracle's estimate from ORACLE_PER_CELL lanes per (system, E bin, v)
+    cell."""
+    wl, out, hist, cells, groups = mixed_run
+    idx = W.stratified(wl, ORACLE_PER_CELL)
+    o = FC.oracle_lanes(wl, idx)
+    dev, ratio = FC.sigma_deviations(wl, groups, idx, o, oracle)
+    worst = np.unravel_index(np.argmax(dev), dev.shape)
+    print(f"\nmixed study: largest |sigma_gpu - sigma_oracle| / SE over {wl.n_groups} groups x 4 "
+          f"channels: {dev.max():.2f} (group {worst[0]}, channel {worst[1]}); oracle-sample SE "
+          f"/ GPU SE {ratio:.1f} on average; oracle sample {len(idx)} lanes")
+    assert dev.max() <= 3.0

@@ -34,9 +34,9 @@ def Q():
     return qcams
 
 
-def _run(Q, wl, entry, persistent):
+def _run(Q, wl, entry, persistent, **integ_kw):
     import torch
-    integ = Q.make_integ(**wl.integ, persistent=persistent)
+    integ = Q.make_integ(**dict(wl.integ, **integ_kw), persistent=persistent)
     batch = Q.Batch.empty(wl.n, "cuda", sys_id=wl.sys_id, cell=wl.cell)
     Q.init_states(wl.systems, batch, wl.E, wl.b, wl.v, wl.j, wl.R0, wl.seed, wl.id_offset)
     arr = Q.systems_array(wl.systems)
@@ -58,6 +58,27 @@ def test_noalloc_matches_run_batch_on_two_calls(Q):
         assert np.all(np.isin(got["status"], [2, 3, 8])), got["status"]
         for k in FIELDS:
             assert np.array_equal(got[k], ref[k]), k
+
+
+def test_noalloc_fp32_and_fixed_step(Q):
+    """The FP32 integrator (its own refill-queue head in the shared scratch;
+    persistent and one thread per lane, Morse and mixed systems) and the
+    fixed-step mode (no analysis) give the same bits as qcams_run_batch."""
+    plain, mixed = W.plain_h2_ca(per_b=12), W.mixed_ca_h(n=120, seed=6)
+    cases = [(plain, True, dict(W.INTEG_FP32, precision=32)),
+             (mixed, True, dict(W.INTEG_FP32, precision=32)),
+             (plain, False, dict(W.INTEG_FP32, precision=32)),
+             (plain, False, dict(fixed_step=True, h_fixed=0.5, max_steps=300)),
+             (mixed, False, dict(fixed_step=True, h_fixed=0.5, max_steps=300))]
+    for wl, persistent, kw in cases:
+        ref = _run(Q, wl, "qcams_run_batch", persistent, **kw)
+        got = _run(Q, wl, "qcams_run_batch_noalloc", persistent, **kw)
+        if kw.get("fixed_step"):
+            assert np.all(np.isin(got["status"], [1, 8])), got["status"]
+        else:
+            assert np.all(np.isin(got["status"], [2, 3, 8])), got["status"]
+        for k in FIELDS:
+            assert np.array_equal(got[k], ref[k]), (k, kw, persistent)
 
 
 def test_noalloc_rejects_too_many_systems(Q):
@@ -85,18 +106,31 @@ _CHILD = textwrap.dedent("""
     batch.status.copy_(torch.as_tensor(src["status0"]))
     integ = Q.make_integ(**wl.integ, persistent=True)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
     rc = Q.lib().qcams_run_batch_noalloc(Q.systems_array(wl.systems), len(wl.systems),
                                          C.byref(integ), C.byref(batch.c), stream)
     assert rc == 0, rc
     torch.cuda.synchronize()
-    np.savez(sys.argv[3], **batch.host())
+    # the library's per-device context (its cudaMalloc'd scratch) was never created
+    assert not Q.debug_context_exists()
+    out = batch.host()
+    # a second call on the same lanes (now finished) allocates nothing either
+    free0 = torch.cuda.mem_get_info()[0]
+    rc = Q.lib().qcams_run_batch_noalloc(Q.systems_array(wl.systems), len(wl.systems),
+                                         C.byref(integ), C.byref(batch.c), stream)
+    assert rc == 0, rc
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert not Q.debug_context_exists()
+    np.savez(sys.argv[3], **out)
 """)
 
 
 def test_noalloc_as_the_first_call_of_a_process(Q, tmp_path):
-    """In a fresh process whose only library call is qcams_run_batch_noalloc
-    (no per-device context exists), the results equal qcams_run_batch's on
-    the same initial states."""
+    """In a fresh process whose only library calls are
+    qcams_run_batch_noalloc, the results equal qcams_run_batch's on the
+    same initial states, and the library's per-device context (the scratch
+    qcams_run_batch allocates with cudaMalloc) is never created."""
     import torch
     wl = W.plain_h2_ca(per_b=12)
     batch = Q.Batch.empty(wl.n, "cuda", sys_id=wl.sys_id, cell=wl.cell)
