@@ -334,6 +334,18 @@ int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells,
                       int64_t* hist_out, double* xsec_out, void* cuda_stream);
 
 /*
+ * Cross sections from histograms already on the host (Sec. 2.3, Eqs. 13-16;
+ * Sec. 4, Eq. 18): the same per-cell opacities, errors and per-group
+ * sigma / SE as qcams_reduce_xsec writes to xsec_out, computed from a host
+ * copy of the histogram records hist[cells->n_cells][QCAMS_H_STRIDE] (for
+ * example the int64 sum of several shards' histograms, which is exact).
+ * Host-only and synchronous: no device, no stream.  Same limits as
+ * qcams_reduce_xsec; cells->b, cells->w (and cells->group if n_groups > 0)
+ * are required.
+ */
+int qcams_xsec_from_hist(const int64_t* hist, const qcams_cells* cells, double* xsec_out);
+
+/*
  * qcams_run_batch without any device allocation.  The paper has no
  * counterpart: this is a deployment variant for callers that cannot call
  * cudaMalloc (an application whose device memory all comes from its own pool

@@ -805,34 +805,9 @@ int qcams_analyze(const qcams_system* sys, int32_t n_sys, const qcams_integ* int
   return cuda_status(cudaGetLastError());
 }
 
-int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_t* hist_out,
-                      double* xsec_out, void* cuda_stream) {
-  clear_stale_error();
-  if (!batch || !cells || !hist_out || batch->n < 0) return QCAMS_E_INVALID;
-  if (cells->n_cells < 1 || cells->n_groups < 0) return QCAMS_E_INVALID;
-  if (cells->n_cells > kMaxCells || cells->n_groups > kMaxCells) return QCAMS_E_CAPACITY;
-  if (batch->n > 0 && (!batch->cell || !batch->cls || !batch->vt || !batch->jt || !batch->gbw))
-    return QCAMS_E_INVALID;
-  if (cells->weighted && !batch->isw) return QCAMS_E_INVALID;
-  if (xsec_out && (!cells->b || !cells->w || (cells->n_groups > 0 && !cells->group)))
-    return QCAMS_E_INVALID;
-  int rc;
-  if ((rc = check_device()) != QCAMS_OK) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  const size_t nh = (size_t)cells->n_cells * QCAMS_H_STRIDE;
-  cudaError_t e = cudaMemsetAsync(hist_out, 0, nh * sizeof(int64_t), st);
-  if (e != cudaSuccess) return QCAMS_E_CUDA;
-  if (batch->n > 0) {
-    DevBatch d = dev_batch(batch);
-    const unsigned grid = (unsigned)((batch->n + kReduceChunk - 1) / kReduceChunk);
-    k_reduce<<<grid, kReduceBlock, 0, st>>>(d, cells->n_cells, (unsigned long long*)hist_out);
-    if ((e = cudaGetLastError()) != cudaSuccess) return QCAMS_E_CUDA;
-  }
-  if (!xsec_out) return QCAMS_OK;
-  std::vector<int64_t> H(nh);
-  e = cudaMemcpyAsync(H.data(), hist_out, nh * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return QCAMS_E_CUDA;
+// Cross sections from host histograms (Sec. 2.3 and Sec. 4): shared by
+// qcams_reduce_xsec and qcams_xsec_from_hist.
+static void xsec_finalize(const int64_t* hist, const qcams_cells* cells, double* xsec_out) {
   // Opacity and binomial error per cell (Eqs. 13, 16); cross sections per
   // group as 2 pi sum w b P (Eq. 18 with the angular measure divided out).
   // Entry 6 is the reactive total R_AC + R_BC (exclusive classes, so its
@@ -843,7 +818,7 @@ int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_
   double* grp = xsec_out + 2 * NE * (size_t)nc;
   for (size_t k = 0; k < 2 * NE * (size_t)ng; ++k) grp[k] = 0.0;
   for (int c = 0; c < nc; ++c) {
-    const int64_t* h = H.data() + (size_t)c * QCAMS_H_STRIDE;
+    const int64_t* h = hist + (size_t)c * QCAMS_H_STRIDE;
     double N = 0.0;
     for (int k = 0; k < 5; ++k) N += (double)h[QCAMS_H_COUNT + k];
     for (int k = 0; k < NE; ++k) {
@@ -876,6 +851,46 @@ int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_
   for (int g = 0; g < ng; ++g)
     for (int k = 0; k < NE; ++k)
       grp[2 * NE * (size_t)g + 2 * k + 1] = 2.0 * kPi * std::sqrt(var[NE * (size_t)g + k]);
+}
+
+int qcams_reduce_xsec(const qcams_batch* batch, const qcams_cells* cells, int64_t* hist_out,
+                      double* xsec_out, void* cuda_stream) {
+  clear_stale_error();
+  if (!batch || !cells || !hist_out || batch->n < 0) return QCAMS_E_INVALID;
+  if (cells->n_cells < 1 || cells->n_groups < 0) return QCAMS_E_INVALID;
+  if (cells->n_cells > kMaxCells || cells->n_groups > kMaxCells) return QCAMS_E_CAPACITY;
+  if (batch->n > 0 && (!batch->cell || !batch->cls || !batch->vt || !batch->jt || !batch->gbw))
+    return QCAMS_E_INVALID;
+  if (cells->weighted && !batch->isw) return QCAMS_E_INVALID;
+  if (xsec_out && (!cells->b || !cells->w || (cells->n_groups > 0 && !cells->group)))
+    return QCAMS_E_INVALID;
+  int rc;
+  if ((rc = check_device()) != QCAMS_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t nh = (size_t)cells->n_cells * QCAMS_H_STRIDE;
+  cudaError_t e = cudaMemsetAsync(hist_out, 0, nh * sizeof(int64_t), st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  if (batch->n > 0) {
+    DevBatch d = dev_batch(batch);
+    const unsigned grid = (unsigned)((batch->n + kReduceChunk - 1) / kReduceChunk);
+    k_reduce<<<grid, kReduceBlock, 0, st>>>(d, cells->n_cells, (unsigned long long*)hist_out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return QCAMS_E_CUDA;
+  }
+  if (!xsec_out) return QCAMS_OK;
+  std::vector<int64_t> H(nh);
+  e = cudaMemcpyAsync(H.data(), hist_out, nh * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return QCAMS_E_CUDA;
+  xsec_finalize(H.data(), cells, xsec_out);
+  return QCAMS_OK;
+}
+
+int qcams_xsec_from_hist(const int64_t* hist, const qcams_cells* cells, double* xsec_out) {
+  if (!hist || !cells || !xsec_out) return QCAMS_E_INVALID;
+  if (cells->n_cells < 1 || cells->n_groups < 0) return QCAMS_E_INVALID;
+  if (cells->n_cells > kMaxCells || cells->n_groups > kMaxCells) return QCAMS_E_CAPACITY;
+  if (!cells->b || !cells->w || (cells->n_groups > 0 && !cells->group)) return QCAMS_E_INVALID;
+  xsec_finalize(hist, cells, xsec_out);
   return QCAMS_OK;
 }
 

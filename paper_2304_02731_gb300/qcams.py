@@ -37,7 +37,7 @@ EXPORTS = ["qcams_status_string", "qcams_system_setup", "qcams_levels", "qcams_i
            "qcams_run_batch", "qcams_analyze", "qcams_reduce_xsec", "qcams_last_run_stats",
            "qcams_fma_peak", "qcams_device_info", "qcams_shutdown", "qcams_run_batch_noalloc",
            "qcams_debug_exp", "qcams_debug_force_math", "qcams_debug_ff_dot",
-           "qcams_debug_context_exists", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
+           "qcams_debug_context_exists", "qcams_xsec_from_hist", "qcams_autotune", "qcams_mlp_init", "qcams_mlp_sync",
            "qcams_mlp_features", "qcams_mlp_fit_standardizer", "qcams_mlp_grad",
            "qcams_mlp_train_step", "qcams_mlp_train", "qcams_mlp_infer", "qcams_build_proposal",
            "qcams_sample_proposal", "qcams_rate_constants", "qcams_gb_distribution"]
@@ -137,6 +137,7 @@ def lib():
                 "qcams_run_batch": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
                 "qcams_analyze": (C.c_int, [P(System), I32, P(Integ), P(CBatch), V]),
                 "qcams_reduce_xsec": (C.c_int, [P(CBatch), P(Cells), V, V, V]),
+                "qcams_xsec_from_hist": (C.c_int, [P(I64), P(Cells), P(D)]),
                 "qcams_last_run_stats": (C.c_int, [P(RunStats), V]),
                 "qcams_fma_peak": (C.c_int, [I32, P(D), V]),
                 "qcams_device_info": (C.c_int, [P(I32), P(I32), P(I32)]),
@@ -406,6 +407,27 @@ def reduce_xsec(batch: Batch, n_cells: int, cell_b=None, cell_w=None, group=None
         return hist, None, None
     return (hist, out[:14 * n_cells].reshape(n_cells, 7, 2),
             out[14 * n_cells:].reshape(n_groups, 7, 2))
+
+
+def xsec_from_hist(hist, cell_b, cell_w, group, n_groups, weighted=False):
+    """qcams_xsec_from_hist: cross sections from host int64 histograms
+    [n_cells, H_STRIDE] (e.g. the merged histograms of several shards).
+    Returns (cells [n_cells, 7, 2], groups [n_groups, 7, 2])."""
+    h = np.ascontiguousarray(hist, np.int64).reshape(-1, H_STRIDE)
+    n_cells = h.shape[0]
+    cells = Cells()
+    cells.n_cells = int(n_cells)
+    cells.n_groups = int(n_groups)
+    cb = np.ascontiguousarray(cell_b, np.float64)
+    cw = np.ascontiguousarray(cell_w, np.float64)
+    cg = np.ascontiguousarray(group, np.int32)
+    cells.b, cells.w, cells.group = cb.ctypes.data, cw.ctypes.data, cg.ctypes.data
+    cells.weighted = int(bool(weighted))
+    out = np.zeros(14 * n_cells + 14 * n_groups)
+    _check(lib().qcams_xsec_from_hist(h.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(cells),
+                                      out.ctypes.data_as(C.POINTER(C.c_double))),
+           "qcams_xsec_from_hist")
+    return out[:14 * n_cells].reshape(n_cells, 7, 2), out[14 * n_cells:].reshape(n_groups, 7, 2)
 
 
 def last_run_stats(stream=None) -> dict:

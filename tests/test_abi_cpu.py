@@ -170,3 +170,26 @@ def test_proposal_spec_limits_without_a_device(Q):
     assert L.qcams_sample_proposal(C.byref(bad), fake, fake, 10, 0, 0, fake, u4, fake, fake,
                                    None) == -1
     assert L.qcams_mlp_train(C.byref(m), fake, fake, 10, 1, 0, 1e-3, 0, fake, None, None) == -1
+
+
+def test_xsec_from_host_histograms_matches_oracle(Q, oracle):
+    """qcams_xsec_from_hist (host, no device): the cross sections of random
+    histogram records equal the oracle's (Sec. 2.3, Eqs. 13-16; Sec. 4) to
+    rounding, plain and importance-weighted; a bad argument is rejected."""
+    rng = np.random.default_rng(12)
+    nc, ng = 40, 5
+    n = 20000
+    cls = rng.choice(6, n, p=[0.55, 0.1, 0.1, 0.15, 0.05, 0.05])
+    cell = rng.integers(0, nc, n)
+    vt, jt = rng.integers(0, 70, n), rng.integers(0, 300, n)
+    gbw, isw = rng.uniform(0, 9, n), rng.uniform(0.2, 5.0, n)
+    H = oracle.reduce(cls, vt, jt, gbw, cell, nc, isw)
+    b, w = rng.uniform(0, 10, nc), rng.uniform(0.1, 1.0, nc)
+    group = rng.integers(-1, ng, nc).astype(np.int32)
+    for weighted in (False, True):
+        cells, groups = Q.xsec_from_hist(H, b, w, group, ng, weighted)
+        oc, og = oracle.xsec(H, b, w, group, ng, weighted)
+        assert np.allclose(cells, oc, rtol=1e-14, atol=0)
+        assert np.allclose(groups, og, rtol=1e-13, atol=1e-300)
+    with pytest.raises(Q.QcamsError):
+        Q.xsec_from_hist(H, b, w, group, 65537)

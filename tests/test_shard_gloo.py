@@ -1,7 +1,9 @@
 """Sharding over ranks (CPU, gloo): the same global trajectory ids split over
-1, 2 or 4 ranks give bit-identical merged histograms, and a rank that dies
-before the merge makes the survivors' collective fail within the timeout
-instead of hanging."""
+1, 2 or 4 ranks give bit-identical merged histograms (per-cell records in
+the library's layout, QCAMS_H_STRIDE int64 per cell) and, through the
+library's host entry point qcams_xsec_from_hist, bit-identical cross
+sections; a rank that dies before the merge makes the survivors' collective
+fail within the timeout instead of hanging."""
 import os
 import socket
 
@@ -41,7 +43,11 @@ def _rank_main(rank, world, port, per_b, out_q, die_rank):
         os._exit(3)                      # this rank dies before the merge
     try:
         shard.merge_histograms(t)
-        out_q.put((rank, "ok", t.numpy().copy()))
+        from paper_2304_02731_gb300 import qcams as Q
+        assert O.H_STRIDE == Q.H_STRIDE
+        cells, groups = Q.xsec_from_hist(t.numpy(), wl.cell_b, wl.cell_w, wl.cell_group,
+                                         wl.n_groups)
+        out_q.put((rank, "ok", (t.numpy().copy(), cells.copy(), groups.copy())))
     except Exception as e:              # the collective reports the dead peer
         out_q.put((rank, "error", type(e).__name__))
     finally:
@@ -91,7 +97,10 @@ def test_sharded_histograms_are_bit_identical(oracle, world):
     assert ref[0] == "ok"
     for r in range(world):
         assert got[r][0] == "ok"
-        assert np.array_equal(got[r][1], ref[1])
+        for a, b in zip(got[r][1], ref[1]):      # histograms, per-cell and per-group xsec
+            assert np.array_equal(a, b)
+    # sigma_Q of the plain study: every separated lane is a quench
+    assert ref[1][2][0, 0, 0] > 0
 
 
 def test_dead_rank_fails_the_merge_instead_of_hanging(oracle):
