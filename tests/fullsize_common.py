@@ -90,8 +90,9 @@ def sigma_deviations(wl, groups, idx, res, oracle, classes=(0, 1, 2, 3)):
     oracle's estimate from the sampled lanes idx (outcomes res) and SE the
     two estimates' standard errors combined.  A count of 0 or N has a zero
     binomial error; the sample's error is bounded with the count clipped to
-    [1, N - 1].  Returns (deviations [n_groups][len(classes)], the mean
-    ratio of the oracle sample's SE to the GPU's)."""
+    [1, N - 1].  Returns (deviations [n_groups][len(classes)], the median
+    ratio of the oracle sample's SE to the GPU's over the non-degenerate
+    entries)."""
     cls_o = res["cls"]
     zeros = np.zeros(len(idx), np.int32)
     h_o = oracle.reduce(cls_o, zeros, zeros, np.zeros(len(idx)), wl.cell[idx], wl.n_cells)
@@ -108,6 +109,6 @@ def sigma_deviations(wl, groups, idx, res, oracle, classes=(0, 1, 2, 3)):
             se_o = max(g_o[g, k, 1], se_o)
             se = math.hypot(groups[g, k, 1], se_o)
             dev[g, col] = abs(groups[g, k, 0] - g_o[g, k, 0]) / se if se > 0 else 0.0
-            if groups[g, k, 1] > 0:
-                ratios.append(se_o / groups[g, k, 1])
-    return dev, float(np.mean(ratios)) if ratios else float("nan")
+            if groups[g, k, 1] > 0 and g_o[g, k, 1] > 0:
+                ratios.append(g_o[g, k, 1] / groups[g, k, 1])
+    return dev, float(np.median(ratios)) if ratios else float("nan")

@@ -33,21 +33,30 @@ def full_run():
 @pytest.fixture(scope="module")
 def sampled_lanes(full_run):
     """1,000 lanes drawn across the whole sweep, each re-run by the oracle
-    from the same (seed, id)."""
+    from the same (seed, id), and once more by the oracle with its relative
+    tolerance changed by one part in 10^9 (a perturbation far below the
+    method's own accuracy, the size of the step-size differences between two
+    valid implementations)."""
     wl = full_run[0]
     idx = np.sort(np.random.default_rng(0).choice(wl.n, 1000, replace=False))
-    return idx, FC.oracle_lanes(wl, idx)
+    pert = dict(wl.integ, rtol=wl.integ["rtol"] * (1.0 + 1e-9))
+    return idx, FC.oracle_lanes(wl, idx), FC.oracle_lanes(wl, idx, pert)
 
 
 def test_full_size_sampled_lanes_match_oracle(full_run, sampled_lanes):
     """Outcome classes on 1,000 sampled lanes.  Lanes that reached a product
     (stopped by r_stop on both sides) agree for >= 99 %.  A lane still inside
     a complex at t_max has no product yet: its class is a snapshot of a
-    chaotic orbit, so the t_max share is reported and the agreement over
-    all lanes is held to 1 - (t_max share) - 1 %.  Energy conservation
-    matches the oracle's lane by lane."""
+    chaotic orbit, and whether a long-lived complex breaks up before t_max
+    depends on rounding-level details of the integration.  The oracle shows
+    this against itself: with its tolerance changed by 1e-9 it disagrees
+    with its own classes on such lanes.  So the agreement over all lanes is
+    held to 1 - (t_max share) - 1 % and to the oracle's self-agreement minus
+    2 %.  Energy conservation matches the oracle's lane by lane."""
     wl, out, hist, cells, groups = full_run
-    idx, o = sampled_lanes
+    idx, o, o2 = sampled_lanes
+    self_agree = np.mean(o["cls"] == o2["cls"])
+    self_done = (o["status"] == 2) & (o2["status"] == 2)
     g_st, g_cls = out["status"][idx], out["cls"][idx]
     done = (g_st == 2) & (o["status"] == 2)
     tmax = (g_st == 3) | (o["status"] == 3)
@@ -60,9 +69,12 @@ def test_full_size_sampled_lanes_match_oracle(full_run, sampled_lanes):
     print(f"\nsampled lanes: class agreement {agree.mean():.4f} over all {len(idx)}, "
           f"{agree[done].mean():.4f} over the {done.sum()} that reached a product on both "
           f"sides; t_max share {tmax.mean():.4f} (GPU {np.mean(g_st == 3):.4f}, oracle "
-          f"{np.mean(o['status'] == 3):.4f}); both at t_max {np.mean((g_st == 3) & (o['status'] == 3)):.4f}")
+          f"{np.mean(o['status'] == 3):.4f}); both at t_max {np.mean((g_st == 3) & (o['status'] == 3)):.4f}"
+          f"\noracle against itself (rtol x (1 + 1e-9)): class agreement {self_agree:.4f} over all, "
+          f"{np.mean(o['cls'][self_done] == o2['cls'][self_done]):.4f} over {self_done.sum()} product lanes")
     assert agree[done].mean() >= 0.99
     assert agree.mean() >= 1.0 - tmax.mean() - 0.01
+    assert agree.mean() >= self_agree - 0.02
     # energy conservation: the same order as the oracle's on every lane
     scale = np.maximum(np.abs(o["E0"]), wl.E[idx])
     e_g = np.abs(out["dE"][idx]) / scale
@@ -110,7 +122,7 @@ def test_full_size_cross_sections_within_3se_of_oracle(full_run, oracle_sample, 
     wl, out, hist, cells, groups = full_run
     dev, ratio = FC.sigma_deviations(wl, groups, *oracle_sample, oracle)
     print(f"\nlargest |sigma_gpu - sigma_oracle| / SE over 16 energies x 4 channels: "
-          f"{dev.max():.2f}; oracle-sample SE / GPU SE {ratio:.1f} on average")
+          f"{dev.max():.2f}; oracle-sample SE / GPU SE {ratio:.1f} (median)")
     assert dev.max() <= 3.0
 
 

@@ -57,6 +57,15 @@ def _setup(Q, seed, n):
 
 
 def test_mlp_gradient_matches_oracle(Q, oracle):
+    """Gradient of the softmax cross-entropy per layer against the FP64
+    oracle.  The GPU rounds both operands of every matrix product to BF16
+    (relative error up to u = 2^-9, standard deviation u / sqrt(3) per
+    element), so a product of non-cancelling sums carries a relative error of
+    about u sqrt(2/3); the first layer's gradient sits at the end of the
+    longest chain of such products (4 forward, 3 backward, the outer product
+    with the inputs: 8), about sqrt(8) u sqrt(2/3) = 4.5e-3.  The bound
+    2^-7 = 4u per layer leaves a factor ~1.7 over that; the direction must
+    agree to cos > 0.9995."""
     import torch
     n = 2000
     mlp, p, x, xs, xd = _setup(Q, 3, n)
@@ -70,7 +79,7 @@ def test_mlp_gradient_matches_oracle(Q, oracle):
         rel = np.linalg.norm(ga - go) / np.linalg.norm(go)
         cos = ga @ go / (np.linalg.norm(ga) * np.linalg.norm(go))
         print(f"\n{name}: rel {rel:.3e} cos {cos:.6f}")
-        assert rel < 0.05 and cos > 0.998, name
+        assert rel < 2.0 ** -7 and cos > 0.9995, name
 
 
 def test_mlp_inference_matches_oracle(Q, oracle):

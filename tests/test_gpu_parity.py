@@ -726,11 +726,12 @@ def _constructed_rule_lanes(oracle):
 def test_stop_and_collapse_rules_on_constructed_states(Q, oracle):
     """The stop rules and the Buckingham collapse on the constructed lanes
     that the oracle pins against scipy: the GPU ends every lane with the
-    oracle's status and on the same accepted step.  FP64 (one thread per
-    lane and persistent; Buckingham / mixed systems run the generic force
-    kernel, the all-Morse batch the Morse kernel) at the study's tolerances,
-    and the FP32 integrator at its own (1e-6 / 1e-8) against the oracle at
-    the same tolerances."""
+    oracle's status and, in FP64, on the same accepted step.  FP64 (one
+    thread per lane and persistent; Buckingham / mixed systems run the
+    generic force kernel, the all-Morse batch the Morse kernel) at the
+    study's tolerances, and the FP32 integrator at its own (1e-6 / 1e-8)
+    against the oracle at
+    the same tolerances (same status; its own step sequence, see below)."""
     import torch
     specs, osys, lanes = _constructed_rule_lanes(oracle)
     groups = [("generic", [0, 1, 2], lanes),
@@ -759,10 +760,22 @@ def test_stop_and_collapse_rules_on_constructed_states(Q, oracle):
                 g = b.host()
                 print(f"\nFP{prec} {name} persistent={persistent}: status "
                       f"{list(g['status'])} / oracle {list(o['status'])}; nsteps "
-                      f"{list(g['nsteps'])} / {list(o['nsteps'])}")
+                      f"{list(g['nsteps'])} / {list(o['nsteps'])}; t "
+                      f"{[round(float(x), 4) for x in g['t']]} / "
+                      f"{[round(float(x), 4) for x in o['t']]}")
                 assert np.array_equal(g["status"], o["status"]), (prec, name, persistent)
                 assert np.array_equal(g["cls"][g["status"] == 7], np.full((g["status"] == 7).sum(), 5))
-                assert np.array_equal(g["nsteps"], o["nsteps"]), (prec, name, persistent)
+                if prec == 64:
+                    assert np.array_equal(g["nsteps"], o["nsteps"]), (prec, name, persistent)
+                else:
+                    # the FP32 integrator forms its error estimate from FP32
+                    # stages (rounding ~1e-7 against rtol 1e-6), so its step
+                    # sequence is its own: the rule fires at the same event,
+                    # the stop time within a few of its steps
+                    first = g["nsteps"] == 1
+                    assert np.array_equal(first, o["nsteps"] == 1)
+                    rel = np.abs(g["t"] - o["t"]) / o["t"]
+                    assert np.all(rel[~first] < 0.05), rel
             if name == "generic":
                 expect = [2, 7, 7, 7, 7] * 2 + [7, 2] + [2] * 6
                 assert list(o["status"]) == expect, list(o["status"])
