@@ -35,35 +35,58 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# FP64 floating-point operations per attempted integrator step of the Morse
-# kernel: 2 dfma + dmul + dadd, from ncu sass counters on the profile case
-# (profiles/k_integrate_plain_sweep_3840lanes_3000steps.md): 342 DFMA,
-# 137 DMUL, 37 DADD per lane-step, six right-hand sides included.  The FP64
-# pipe issues 342 + 137 + 37 = 516 instructions per step; the DFMA-chain
-# peak runs one DFMA (2 FLOP) per pipe slot, so pipe_frac below is the
-# fraction of the pipe's instruction rate the kernel uses.
+# Per-step operation counts of the integrators' Morse kernels, from ncu's
+# sass counters (smsp__sass_thread_inst_executed_op_{dfma,dmul,dadd,ffma,
+# fmul,fadd}_pred_on.sum and smsp__sass_thread_inst_executed.sum, divided by
+# the launch's attempted lane-steps) on the 3,840-lane sweep subset capped
+# at 3,000 attempts (bench.py --lanes 4096 --max-steps 3000 --persistent 0).
+# Each set holds the SHA-256 of the kernel sources it was measured on; the
+# bench recomputes it and marks the roofline's counts stale when the
+# sources have changed since.
+#   FP64: 342 DFMA + 137 DMUL + 37 DADD per step (six right-hand sides
+#   included) = 516 FP64-pipe instructions, 858 FLOP (DFMA = 2).  The
+#   DFMA-chain peak runs one DFMA per pipe slot, so pipe_frac below is the
+#   fraction of the FP64 pipe's instruction rate the kernel uses.
 FP64_FLOP_PER_STEP = 858
 FP64_INSTR_PER_STEP = 516
-# FP32 floating-point operations per attempted step of the FP32 Morse kernel
-# (2 ffma + fmul + fadd from ncu sass counters on the same profile case,
-# profiles/k_integrate32_plain_sweep_3840lanes_3000steps.md: 392 FFMA,
-# 225 FMUL, 39 FADD per lane-step); it also issues one DADD (the time).  The
-# kernel is bound by instruction issue: 946 thread instructions per step
-# (all pipes), so issue_frac below is the fraction of the SMs' issue rate
-# (4 warp instructions per SM per cycle) it uses.
+#   FP32: 392 FFMA + 225 FMUL + 39 FADD = 1,049 FLOP and one DADD (the
+#   time) in 946 thread instructions per step (all pipes); the kernel is
+#   bound by instruction issue, so issue_frac below is the fraction of the
+#   SMs' issue rate (4 warp instructions per SM per cycle) it uses.
 FP32_FLOP_PER_STEP = 1049
 FP32_THREAD_INSTR_PER_STEP = 946
+KERNEL_SOURCES = {
+    64: ["integrate.cu", "elem64.cuh", "ff.cuh", "texp.cuh", "exp2_table.inc",
+         "dp5_tableau.cuh"],
+    32: ["integrate32.cu", "dp5_tableau.cuh"],
+}
+COUNTS_SOURCE_SHA256 = {
+    64: "0d05ce86c76924d20f2f466b4986810db919333d08f23b8a62f307e96a7b9f5a",
+    32: "1fb9ae68cc916bd3b938ea3268241c0788d3c79679dea927580d0c265ac95ec5",
+}
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the FP64 profile case (1,219,840 B read, nothing
-# written back during the launch, for 3,840 lanes), per lane: the state is
-# loaded once, everything else is in registers; the 16 KB exponential table
-# is read from DRAM once and served from L2 to the other blocks.  The figure
-# also holds the fetch of the kernel's code (it moved with the code size
-# between kernel versions: 0.68-1.2 MB), a fixed cost per launch.
+# dram__bytes_write.sum of the same FP64 profile case (1,219,840 B read,
+# nothing written back during the launch, for 3,840 lanes), per lane: the
+# state is loaded once, everything else is in registers; the 16 KB
+# exponential table is read from DRAM once and served from L2 to the other
+# blocks.  The figure also holds the fetch of the kernel's code, a fixed
+# cost per launch.
 DRAM_BYTES_PER_LANE = 1219840 / 3840
 # The same for the FP32 kernel (560,896 B read, no table): its state is
 # loaded as (value, compensation) pairs from the same FP64 arrays.
 DRAM_BYTES_PER_LANE_FP32 = 560896 / 3840
+
+
+def kernel_sources_sha256(precision: int) -> str:
+    """SHA-256 over the integrator sources whose instruction counts the
+    constants above record."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2304_02731_gb300", "csrc")
+    for f in KERNEL_SOURCES[precision]:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def parse():
@@ -78,6 +101,9 @@ def parse():
                     help="learned: trajectories generated to train the network")
     ap.add_argument("--is-lanes", type=int, default=200_000,
                     help="learned: trajectories per estimate (proposal and uniform)")
+    ap.add_argument("--train-precision", type=int, default=32, choices=[64, 32],
+                    help="learned: integrator of the training trajectories (the estimates "
+                         "are always FP64)")
     ap.add_argument("--per-cell", type=int, default=8192,
                     help="sweep: trajectories per (E, b) cell")
     ap.add_argument("--lanes", type=int, default=0,
@@ -424,6 +450,12 @@ def run_ours(args):
                             issue_frac=rate / issue)
     else:
         roofline.update(achieved=None, frac=None)
+    counts_current = kernel_sources_sha256(args.precision) == COUNTS_SOURCE_SHA256[args.precision]
+    roofline.update(counts_current=counts_current,
+                    counts_note=("per-step counts measured on these kernel sources"
+                                 if counts_current else
+                                 "kernel sources changed since the per-step counts were "
+                                 "measured: achieved / frac use stale counts"))
     roofline.update(steps_per_launch=steps_per_launch, integrate_ms=avg_integ_ms,
                     analyze_ms=float(np.mean(analyze_ms)),
                     rest_of_step_ms=ms_max / args.steps - avg_integ_ms,
@@ -485,8 +517,11 @@ def run_learned(args):
     its standard error and GPU time, and FOM = 1 / (SE^2 T); the ratio of
     FOMs is the gain in standard error per GPU-second at equal accuracy.
 
-    The network costs C = (training-data generation + training) seconds
-    once.  Spread over K estimates, an estimate costs T_is + C / K, so its
+    The training trajectories are integrated with the FP32 integrator by
+    default (--train-precision 32): their classes only shape the proposal,
+    and every estimate integrates its own lanes in FP64, so the estimator is
+    unbiased whatever the labels.  The network costs C = (training-data
+    generation + training) seconds once.  Spread over K estimates, an estimate costs T_is + C / K, so its
     amortised FOM ratio is G_K = FOM_u^-1 / (SE_is^2 (T_is + C / K)) and
     the learned proposal wins end to end from K* = C / (T_is (G - 1))
     estimates on (G the per-estimate ratio).  Both are reported, with K = 3
@@ -503,7 +538,8 @@ def run_learned(args):
     clocks.start()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x, cls, host = L.generate(spec_sys, args.train_lanes, seed=101)
+    x, cls, host = L.generate(spec_sys, args.train_lanes, seed=101,
+                              precision=args.train_precision)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
     mlp = Q.MLP(seed=1)
@@ -540,7 +576,8 @@ def run_learned(args):
             "higher_is_better": True, "n_gpus": 1, "dtype": "f64 integration, bf16 network",
             "data": "synthetic",
             "config": {"workload": "LJ(12,6) Ca-H + H2, mixed-study lanes", "train_lanes":
-                       args.train_lanes, "is_lanes_per_estimate": args.is_lanes,
+                       args.train_lanes, "train_precision": f"FP{args.train_precision}",
+                       "is_lanes_per_estimate": args.is_lanes,
                        "state": {"v": v, "j": j, "train_reactive_fraction": frac}},
             "training": {"generate_s": t_gen, "train_s": t_train, "loss_first": losses[0],
                          "loss_last": losses[-1], "epochs": len(losses)},

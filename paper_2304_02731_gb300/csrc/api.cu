@@ -140,8 +140,15 @@ int make_sysset(const qcams_system* sys, int32_t n_sys, SysSet* out) {
     d.mu_pair[1] = mB * mC / (mB + mC);
     d.mu_pair[2] = mC * mA / (mC + mA);
     for (int k = 0; k < 3; ++k) {
+      d.inv_mu_pair[k] = 1.0 / d.mu_pair[k];
+      d.s2mu_pi[k] = std::sqrt(2.0 * d.mu_pair[k]) / 3.14159265358979323846;
+    }
+    for (int k = 0; k < 3; ++k) {
       int rc = make_devpair(in.pair[k], &d.pair[k]);
       if (rc != QCAMS_OK) return rc;
+      DevPair& q = d.pair[k];
+      const double c[5] = {q.c0, q.c1, q.c2, q.c3, q.c4};
+      for (int i = 0; i < 5; ++i) q.cf[i] = (float)c[i];
     }
     // dP1/dt = -(u0 r_AB - cB u1 r_BC + cA u2 r_CA), dP2/dt = -(u1 r_BC + u2 r_CA)
     d.kf[0] = -d.inv_mu12;
@@ -302,8 +309,8 @@ __device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu,
   const double s2mu = sqrt(2.0 * mu);
   double lo = Vmin, hi = Etop - 1e-10 * (Etop - Vmin);
   double rm, rp, act, per;
-  if (!turning_points<false>(q, sh, mu, L2, hi, r_min, r_top, nullptr, &rm, &rp)) return L;
-  action_period<kGL128, false, true>(q, mu, L2, hi, rm, rp, nullptr, &act, &per);
+  if (!turning_points<false>(q, sh, mu, 0.0, L2, hi, r_min, r_top, nullptr, &rm, &rp)) return L;
+  action_period<kGL128, false, true>(q, mu, 0.0, L2, hi, rm, rp, nullptr, &act, &per);
   if (-0.5 + s2mu / kPi * act < v) return L;
   // harmonic first guess
   double k2 = pot_d2V(q, r_min) + 3.0 * L2 / (mu * r_min * r_min * r_min * r_min);
@@ -311,8 +318,8 @@ __device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu,
   if (!(E > lo && E < hi)) E = 0.5 * (lo + hi);
   bool ok = false;
   for (int it = 0; it < 200; ++it) {
-    if (!turning_points<false>(q, sh, mu, L2, E, r_min, r_top, nullptr, &rm, &rp)) break;
-    action_period<kGL128, false, true>(q, mu, L2, E, rm, rp, nullptr, &act, &per);
+    if (!turning_points<false>(q, sh, mu, 0.0, L2, E, r_min, r_top, nullptr, &rm, &rp)) break;
+    action_period<kGL128, false, true>(q, mu, 0.0, L2, E, rm, rp, nullptr, &act, &per);
     const double f = -0.5 + s2mu / kPi * act - v;
     if (f < 0) lo = E; else hi = E;
     double En = E - f * 2.0 * kPi / (s2mu * per);
@@ -325,8 +332,8 @@ __device__ DevLevel solve_level(const DevPair& q, const DevShape& sh, double mu,
     E = En;
   }
   if (!ok) return L;
-  if (!turning_points<false>(q, sh, mu, L2, E, r_min, r_top, nullptr, &rm, &rp)) return L;
-  action_period<kGL128, false, true>(q, mu, L2, E, rm, rp, nullptr, &act, &per);
+  if (!turning_points<false>(q, sh, mu, 0.0, L2, E, r_min, r_top, nullptr, &rm, &rp)) return L;
+  action_period<kGL128, false, true>(q, mu, 0.0, L2, E, rm, rp, nullptr, &act, &per);
   L.E = E;
   L.r_minus = rm;
   L.r_plus = rp;
@@ -462,11 +469,11 @@ __global__ void k_init(SysSet sys, const DevLevel* levels, const double* E_col, 
 // Product analysis (Sec. 2.2): one thread per lane (analysis.cuh).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_analyze(SysSet sys, const DevShape* shapes,
-                                                 double gb_sigma, DevBatch B) {
+                                                 double gb_c1, double gb_c2, DevBatch B) {
   __shared__ double sT[kExpTableSize];
   load_exp_table(sT);
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < B.n) analyze_lane(sys, shapes, gb_sigma, B, i, sT);
+  if (i < B.n) analyze_lane(sys, shapes, gb_c1, gb_c2, B, i, sT);
 }
 
 // ---------------------------------------------------------------------------
@@ -584,7 +591,8 @@ cudaError_t launch_shapes(const SysSet& ss, DevShape* shapes, cudaStream_t st) {
 cudaError_t launch_analyze(const SysSet& ss, const DevShape* shapes, double gb_sigma,
                            const DevBatch& d, cudaStream_t st) {
   if (d.n == 0) return cudaSuccess;
-  k_analyze<<<(unsigned)((d.n + 127) / 128), 128, 0, st>>>(ss, shapes, gb_sigma, d);
+  const double c1 = 0.5 / (gb_sigma * gb_sigma), c2 = 1.0 / (gb_sigma * std::sqrt(2.0 * 3.14159265358979323846));
+  k_analyze<<<(unsigned)((d.n + 127) / 128), 128, 0, st>>>(ss, shapes, c1, c2, d);
   return cudaGetLastError();
 }
 
@@ -778,8 +786,7 @@ int qcams_run_batch(const qcams_system* sys, int32_t n_sys, const qcams_integ* i
     return cuda_status(e);
   }
   e = record_event(ctx->ev[2], st);
-  k_analyze<<<(unsigned)((batch->n + 127) / 128), 128, 0, st>>>(ss, ctx->shapes, ip.gb_sigma, d);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_analyze(ss, ctx->shapes, ip.gb_sigma, d, st);
   if (e == cudaSuccess) e = record_event(ctx->ev[3], st);
   ctx->timed = e == cudaSuccess;
   return cuda_status(e);
@@ -801,8 +808,7 @@ int qcams_analyze(const qcams_system* sys, int32_t n_sys, const qcams_integ* int
   DevBatch d = dev_batch(batch);
   k_pair_shapes<<<1, 32, 0, st>>>(ss, ctx->shapes);
   const double sg = integ->gb_sigma > 0 ? integ->gb_sigma : 0.1 / (2.0 * std::sqrt(2.0 * std::log(2.0)));
-  k_analyze<<<(unsigned)((batch->n + 127) / 128), 128, 0, st>>>(ss, ctx->shapes, sg, d);
-  return cuda_status(cudaGetLastError());
+  return cuda_status(launch_analyze(ss, ctx->shapes, sg, d, st));
 }
 
 // Cross sections from host histograms (Sec. 2.3 and Sec. 4): shared by

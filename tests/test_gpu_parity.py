@@ -140,13 +140,27 @@ def _adaptive_pair(Q, oracle, wl, integ_kw=None, persistent=False):
 
 
 def test_adaptive_plain_study_parity(Q, oracle):
-    """200 lanes of the plain H2 + Ca study (E = 0.1, b = 0..6)."""
+    """200 lanes of the plain H2 + Ca study (E = 0.1, b = 0..6).  Every lane
+    that separated on both sides is a quench on both.  Lanes that form a
+    long-lived Ca-H2 complex can still be inside it at t_max: whether such a
+    complex breaks up before t_max depends on rounding-level details, so the
+    all-lane class agreement is held to the oracle's agreement with itself
+    under a 1e-9 change of its tolerance, less 2 %."""
     wl = W.plain_h2_ca(per_b=40)
     batch, g, hist, cells, groups, st, res = _adaptive_pair(Q, oracle, wl)
+    pert = oracle.make_integ(**dict(wl.integ, rtol=wl.integ["rtol"] * (1.0 + 1e-9)))
+    _, res2 = oracle.run_lanes(_osys(oracle, wl.systems), wl.sys_id, wl.E, wl.b, wl.v, wl.j,
+                               wl.R0, wl.seed, pert, wl.id_offset)
     agree = np.mean(g["cls"] == res["cls"])
+    self_agree = np.mean(res2["cls"] == res["cls"])
+    done = (g["status"] == 2) & (res["status"] == 2)
     steps_rel = np.abs(g["nsteps"] - res["nsteps"]) / res["nsteps"]
-    print(f"\nclass agreement {agree:.4f}; median |dnsteps|/nsteps {np.median(steps_rel):.2e}")
-    assert agree >= 0.99
+    print(f"\nclass agreement {agree:.4f} (oracle with itself {self_agree:.4f}); on the "
+          f"{done.sum()} lanes that separated on both sides {np.mean(g['cls'][done] == res['cls'][done]):.4f}; "
+          f"t_max share GPU {np.mean(g['status'] == 3):.3f}, oracle {np.mean(res['status'] == 3):.3f}; "
+          f"median |dnsteps|/nsteps {np.median(steps_rel):.2e}")
+    assert np.all(g["cls"][done] == res["cls"][done])
+    assert agree >= self_agree - 0.02
     assert np.median(steps_rel) < 0.01
     rel = np.abs(g["dE"]) / np.maximum(np.abs(g["E0"]), wl.E)
     assert np.all(rel[g["status"] == 2] < 1e-8)
@@ -771,11 +785,11 @@ def test_stop_and_collapse_rules_on_constructed_states(Q, oracle):
                     # the FP32 integrator forms its error estimate from FP32
                     # stages (rounding ~1e-7 against rtol 1e-6), so its step
                     # sequence is its own: the rule fires at the same event,
-                    # the stop time within a few of its steps
+                    # within one step of the oracle's stop (the last step is
+                    # at most 5 times the next proposed one)
                     first = g["nsteps"] == 1
                     assert np.array_equal(first, o["nsteps"] == 1)
-                    rel = np.abs(g["t"] - o["t"]) / o["t"]
-                    assert np.all(rel[~first] < 0.05), rel
+                    assert np.all(np.abs(g["t"] - o["t"]) <= 10.0 * g["h"]), (g["t"], o["t"], g["h"])
             if name == "generic":
                 expect = [2, 7, 7, 7, 7] * 2 + [7, 2] + [2] * 6
                 assert list(o["status"]) == expect, list(o["status"])
