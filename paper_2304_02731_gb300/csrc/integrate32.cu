@@ -54,11 +54,21 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+// 2^x (one MUFU instruction, relative error about 2^-22): the force law's
+// exponentials e^y are taken as 2^(y log2 e) with the constants of y
+// pre-scaled by log2 e on the host, so no multiply precedes the MUFU.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // FP32 copies of the per-system constants (built on the host, so the kernel
 // never converts doubles in its inner loop).
 struct PairF {
   int kind, m, n, pad;
   float c0, c1, c2, c3, c4;
+  float l0, l1;   // exponent constants times log2 e: Morse c0, c1; Buckingham c1 (l1)
 };
 struct SysF {
   float cA, cB, inv_mu12, inv_mu123, mu12, mu123;
@@ -88,17 +98,17 @@ __device__ __forceinline__ float pair_u(const PairF& q, float s) {
   const float ri = rsqrtf(s);
   const float r = s * ri;
   if (MORSE) {
-    const float x = __expf(fmaf(-q.c0, r, q.c1));
+    const float x = ex2_approx(fmaf(-q.l0, r, q.l1));   // e^{-alpha (r - re)}
     return fmaf(-x, x, x) * ri;
   }
   if (q.kind == QCAMS_MORSE) {   // a Morse pair of a mixed system: V'/r = 2 alpha De x (1 - x) / r
-    const float x = __expf(fmaf(-q.c0, r, q.c1));
+    const float x = ex2_approx(fmaf(-q.l0, r, q.l1));
     return q.c2 * fmaf(-x, x, x) * ri;
   }
   const float ri2 = ri * ri;
   if (q.kind == QCAMS_LJ) return (q.c3 * ipowf_(ri, q.n) - q.c2 * ipowf_(ri, q.m)) * ri2;
   const float ri6 = ri2 * ri2 * ri2;
-  return (q.c3 * ri6 * ri - q.c2 * __expf(-q.c1 * r)) * ri;
+  return (q.c3 * ri6 * ri - q.c2 * ex2_approx(-q.l1 * r)) * ri;   // e^{-B r}
 }
 
 template <bool MORSE>
@@ -140,9 +150,11 @@ struct Lane32 {
 
 // One adaptive attempt (SciPy RK45 rules, as in the FP64 integrator), all
 // stages in FP32; the accepted increments are added with compensation.
-template <bool MORSE>
+// ONE: the batch has a single system, so its constants are read with a
+// compile-time index (constant-bank operands, no per-lane indexed loads).
+template <bool MORSE, bool ONE>
 __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& ip, Lane32& L) {
-  const SysF& S = sys.s[L.sid];
+  const SysF& S = sys.s[ONE ? 0 : L.sid];
   {
     const int eh = (__float_as_int(L.h) >> 23) & 0xff;
     const int et = (__double2hiint(L.t) >> 20) & 0x7ff;
@@ -304,7 +316,7 @@ __device__ __forceinline__ bool runnable(int st) {
   return st == QCAMS_LANE_READY || st == QCAMS_LANE_RUNNING;
 }
 
-template <bool MORSE>
+template <bool MORSE, bool ONE>
 __device__ bool load(const SysSetF& sys, const DevShape* shapes, const IntegParams& ip,
                      const DevBatch& B, int64_t i, Lane32& L, unsigned long long& rhs) {
   L.status = B.status[i];
@@ -314,7 +326,7 @@ __device__ bool load(const SysSetF& sys, const DevShape* shapes, const IntegPara
     B.status[i] = QCAMS_LANE_INVALID;
     return false;
   }
-  const SysF& S = sys.s[L.sid];
+  const SysF& S = sys.s[ONE ? 0 : L.sid];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     const double r = B.y[k][i];
@@ -347,8 +359,9 @@ __device__ bool load(const SysSetF& sys, const DevShape* shapes, const IntegPara
   return true;
 }
 
+template <bool ONE>
 __device__ void store(const SysSetF& sys, const DevBatch& B, int64_t i, const Lane32& L) {
-  const SysF& S = sys.s[L.sid];
+  const SysF& S = sys.s[ONE ? 0 : L.sid];
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
     B.y[k][i] = (double)L.rho[k] - (double)L.crho[k];
@@ -374,23 +387,23 @@ __device__ __forceinline__ void flush(unsigned long long rhs, unsigned long long
   }
 }
 
-template <bool MORSE>
+template <bool MORSE, bool ONE>
 __global__ void __launch_bounds__(128) k_integrate32_plain(SysSetF sys, const DevShape* shapes,
                                                            IntegParams ip, DevBatch B,
                                                            unsigned long long* counters) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long rhs = 0, steps = 0;
   Lane32 L;
-  if (i < B.n && load<MORSE>(sys, shapes, ip, B, i, L, rhs)) {
-    while (L.status == QCAMS_LANE_RUNNING) attempt<MORSE>(sys, ip, L);
+  if (i < B.n && load<MORSE, ONE>(sys, shapes, ip, B, i, L, rhs)) {
+    while (L.status == QCAMS_LANE_RUNNING) attempt<MORSE, ONE>(sys, ip, L);
     rhs += 6ull * L.calls;
     steps += L.calls;
-    store(sys, B, i, L);
+    store<ONE>(sys, B, i, L);
   }
   flush(rhs, steps, counters);
 }
 
-template <bool MORSE>
+template <bool MORSE, bool ONE>
 __global__ void __launch_bounds__(128) k_integrate32_persistent(SysSetF sys,
                                                                 const DevShape* shapes,
                                                                 IntegParams ip, DevBatch B,
@@ -413,17 +426,17 @@ __global__ void __launch_bounds__(128) k_integrate32_persistent(SysSetF sys,
         if (k >= B.n) exhausted = true;
         else {
           idx = k;
-          have = load<MORSE>(sys, shapes, ip, B, idx, L, rhs);
+          have = load<MORSE, ONE>(sys, shapes, ip, B, idx, L, rhs);
         }
       }
     }
     if (__all_sync(FULL, exhausted && !have)) break;
     if (have) {
-      attempt<MORSE>(sys, ip, L);
+      attempt<MORSE, ONE>(sys, ip, L);
       if (L.status != QCAMS_LANE_RUNNING) {
         rhs += 6ull * L.calls;
         steps += L.calls;
-        store(sys, B, idx, L);
+        store<ONE>(sys, B, idx, L);
         have = false;
       }
     }
@@ -460,9 +473,36 @@ SysSetF to_float(const SysSet& in) {
       g.c2 = (float)q.c2;
       g.c3 = (float)q.c3;
       g.c4 = (float)q.c4;
+      const double log2e = 1.4426950408889634;
+      g.l0 = (float)(q.c0 * log2e);
+      g.l1 = (float)(q.c1 * log2e);
     }
   }
   return o;
+}
+
+template <bool MORSE, bool ONE>
+cudaError_t launch32(const SysSetF& sf, const DevShape* shapes, const IntegParams& ip,
+                     const DevBatch& b, int persistent, Ctx& ctx, cudaStream_t st) {
+  const int block = 128;
+  if (persistent) {
+    cudaError_t e = cudaMemsetAsync(ctx.counters + 2, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm,
+                                                      k_integrate32_persistent<MORSE, ONE>, block, 0);
+    if (e != cudaSuccess) return e;
+    long long grid = (long long)(per_sm < 1 ? 1 : per_sm) * ctx.sm_count;
+    const long long need_blocks = (b.n + block - 1) / block;
+    if (grid > need_blocks) grid = need_blocks;
+    if (grid < 1) grid = 1;
+    k_integrate32_persistent<MORSE, ONE><<<(unsigned)grid, block, 0, st>>>(sf, shapes, ip, b,
+                                                                          ctx.counters);
+    return cudaGetLastError();
+  }
+  const unsigned grid = (unsigned)((b.n + block - 1) / block);
+  k_integrate32_plain<MORSE, ONE><<<grid, block, 0, st>>>(sf, shapes, ip, b, ctx.counters);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -471,30 +511,12 @@ cudaError_t launch_integrate32(const SysSet& sys, const DevShape* shapes, const 
                                const DevBatch& b, int persistent, Ctx& ctx, cudaStream_t st,
                                bool all_morse) {
   const SysSetF sf = to_float(sys);
-  const int block = 128;
-  if (persistent) {
-    cudaError_t e = cudaMemsetAsync(ctx.counters + 2, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = all_morse ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &per_sm, k_integrate32_persistent<true>, block, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &per_sm, k_integrate32_persistent<false>, block, 0);
-    if (e != cudaSuccess) return e;
-    long long grid = (long long)(per_sm < 1 ? 1 : per_sm) * ctx.sm_count;
-    const long long need_blocks = (b.n + block - 1) / block;
-    if (grid > need_blocks) grid = need_blocks;
-    if (grid < 1) grid = 1;
-    if (all_morse)
-      k_integrate32_persistent<true><<<(unsigned)grid, block, 0, st>>>(sf, shapes, ip, b, ctx.counters);
-    else
-      k_integrate32_persistent<false><<<(unsigned)grid, block, 0, st>>>(sf, shapes, ip, b, ctx.counters);
-    return cudaGetLastError();
-  }
-  const unsigned grid = (unsigned)((b.n + block - 1) / block);
-  if (all_morse) k_integrate32_plain<true><<<grid, block, 0, st>>>(sf, shapes, ip, b, ctx.counters);
-  else k_integrate32_plain<false><<<grid, block, 0, st>>>(sf, shapes, ip, b, ctx.counters);
-  return cudaGetLastError();
+  const bool one = sys.n == 1;
+  if (all_morse)
+    return one ? launch32<true, true>(sf, shapes, ip, b, persistent, ctx, st)
+               : launch32<true, false>(sf, shapes, ip, b, persistent, ctx, st);
+  return one ? launch32<false, true>(sf, shapes, ip, b, persistent, ctx, st)
+             : launch32<false, false>(sf, shapes, ip, b, persistent, ctx, st);
 }
 
 }  // namespace qcams
