@@ -49,12 +49,12 @@ if ROOT not in sys.path:
 #   fraction of the FP64 pipe's instruction rate the kernel uses.
 FP64_FLOP_PER_STEP = 858
 FP64_INSTR_PER_STEP = 516
-#   FP32: 392 FFMA + 225 FMUL + 39 FADD = 1,049 FLOP and one DADD (the
-#   time) in 946 thread instructions per step (all pipes); the kernel is
+#   FP32: 392 FFMA + 207 FMUL + 39 FADD = 1,031 FLOP and one DADD (the
+#   time) in 874 thread instructions per step (all pipes); the kernel is
 #   bound by instruction issue, so issue_frac below is the fraction of the
 #   SMs' issue rate (4 warp instructions per SM per cycle) it uses.
-FP32_FLOP_PER_STEP = 1049
-FP32_THREAD_INSTR_PER_STEP = 946
+FP32_FLOP_PER_STEP = 1031
+FP32_THREAD_INSTR_PER_STEP = 874
 KERNEL_SOURCES = {
     64: ["integrate.cu", "elem64.cuh", "ff.cuh", "texp.cuh", "exp2_table.inc",
          "dp5_tableau.cuh"],
@@ -62,19 +62,19 @@ KERNEL_SOURCES = {
 }
 COUNTS_SOURCE_SHA256 = {
     64: "0d05ce86c76924d20f2f466b4986810db919333d08f23b8a62f307e96a7b9f5a",
-    32: "1fb9ae68cc916bd3b938ea3268241c0788d3c79679dea927580d0c265ac95ec5",
+    32: "f3dd65025e870e50213e8a48fd029b38e5ba13044537446692c6624e00d85b21",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of the same FP64 profile case (1,219,840 B read,
+# dram__bytes_write.sum of the same FP64 profile case (1,110,784 B read,
 # nothing written back during the launch, for 3,840 lanes), per lane: the
 # state is loaded once, everything else is in registers; the 16 KB
 # exponential table is read from DRAM once and served from L2 to the other
 # blocks.  The figure also holds the fetch of the kernel's code, a fixed
 # cost per launch.
-DRAM_BYTES_PER_LANE = 1219840 / 3840
-# The same for the FP32 kernel (560,896 B read, no table): its state is
+DRAM_BYTES_PER_LANE = 1110784 / 3840
+# The same for the FP32 kernel (559,360 B read, no table): its state is
 # loaded as (value, compensation) pairs from the same FP64 arrays.
-DRAM_BYTES_PER_LANE_FP32 = 560896 / 3840
+DRAM_BYTES_PER_LANE_FP32 = 559360 / 3840
 
 
 def kernel_sources_sha256(precision: int) -> str:
@@ -123,6 +123,10 @@ def parse():
                     help="oracle sample for cpu_baseline: lanes per cell")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default sweep run: skip the short measurements of the other "
+                         "workloads (plain study, FP32 sweep, mixed study, learned proposal) "
+                         "that follow the timed region")
     return ap.parse_args()
 
 
@@ -405,7 +409,8 @@ def run_ours(args):
         hhist = torch.empty(wl.n_cells * Q.H_STRIDE, dtype=torch.int64).pin_memory()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        e2e_steps = min(args.steps, 3)   # each full-size step is seconds long
+        for _ in range(e2e_steps):
             batch.sys_id.copy_(hsid, non_blocking=True)
             batch.cell.copy_(hcell, non_blocking=True)
             E_d.copy_(hE, non_blocking=True)
@@ -419,7 +424,8 @@ def run_ours(args):
         barrier()
         wall = time.perf_counter() - t0
         h2d = sum(x.numel() * x.element_size() for x in (hE, hb_, hv, hj, hsid, hcell))
-        e2e = {"value": world * wl.n * args.steps / wall, "unit": "trajectories/s",
+        e2e = {"value": world * wl.n * e2e_steps / wall, "unit": "trajectories/s",
+               "steps": e2e_steps,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(hhist.numel() * 8)}
 
     # roofline of the dominant kernel (the integrator): the FP64 pipe for
@@ -501,6 +507,9 @@ def run_ours(args):
                      "sigma_first_group": groups[0, :, 0].tolist() if groups is not None and
                      len(groups) else None},
     }
+    if (rank == 0 and world == 1 and args.workload == "sweep" and args.precision == 64
+            and not args.no_extras and not args.lanes):
+        line["other_configs"] = run_extras(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -508,7 +517,101 @@ def run_ours(args):
     return 0
 
 
+def time_steps(Q, wl, integ, steps, warmup, dev):
+    """Time `steps` graph replays of init -> integrate -> analyse -> reduce
+    on workload wl after `warmup` eager steps (CUDA events on the launching
+    stream, clocks sampled meanwhile).  Returns a dict of the figures."""
+    import torch
+    batch = Q.Batch.empty(wl.n, dev, sys_id=wl.sys_id, cell=wl.cell, keep_u=False)
+    E_d, b_d = torch.as_tensor(wl.E, device=dev), torch.as_tensor(wl.b, device=dev)
+    v_d, j_d = torch.as_tensor(wl.v, device=dev), torch.as_tensor(wl.j, device=dev)
+    hist = torch.empty(wl.n_cells * Q.H_STRIDE, dtype=torch.int64, device=dev)
+
+    def step():
+        Q.init_states(wl.systems, batch, E_d, b_d, v_d, j_d, wl.R0, wl.seed, wl.id_offset)
+        Q.run_batch(wl.systems, batch, integ)
+        Q.reduce_xsec(batch, wl.n_cells, hist_out=hist, finalize=False)
+
+    for _ in range(max(1, warmup)):
+        step()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    integ_ms, analyze_ms = [], []
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+        st = Q.last_run_stats()
+        integ_ms.append(st["integrate_ms"])
+        analyze_ms.append(st["analyze_ms"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clock_info = clocks.stop()
+    ms = e0.elapsed_time(e1) / steps
+    _, cells, groups = Q.reduce_xsec(batch, wl.n_cells, wl.cell_b, wl.cell_w, wl.cell_group,
+                                     wl.n_groups, hist_out=hist)
+    cls = np.bincount(batch.cls.cpu().numpy(), minlength=6).tolist()
+    return {"workload": wl.name, "trajectories": wl.n, "steps": steps, "warmup": warmup,
+            "value": wl.n / (ms * 1e-3), "unit": "trajectories/s", "ms_per_step": ms,
+            "integrate_ms": float(np.mean(integ_ms)), "analyze_ms": float(np.mean(analyze_ms)),
+            "launch": f"persistent refill queue, CUDA graph, block {integ.block or 128} x "
+                      f"{integ.blocks_per_sm or 1}/SM variant",
+            "cls_counts_Q_RAC_RBC_D_AMBIG_FAIL": cls, "clocks": clock_info}
+
+
+def run_extras(args, dev):
+    """Short measurements of the other workloads after the headline sweep
+    (single GPU, outside its timed region): the 1,000-lane plain study and
+    the 2,000,000-lane mixed study in FP64 (autotuned launch shape), the
+    sweep with the FP32 integrator, and the learned-proposal study."""
+    import torch
+    from paper_2304_02731_gb300 import qcams as Q
+    from paper_2304_02731_gb300 import workloads as W
+    out = {}
+
+    def tuned(wl, integ):
+        per = max(1, min(256, wl.n // wl.n_cells))
+        sw = wl.take(W.stratified(wl, per))
+        sb = Q.Batch.empty(sw.n, dev, sys_id=sw.sys_id, cell=sw.cell, keep_u=False)
+        Q.init_states(sw.systems, sb, sw.E, sw.b, sw.v, sw.j, sw.R0, sw.seed, sw.id_offset)
+        best, _ = Q.autotune(sw.systems, sb, integ, max_attempts=1500)
+        return best
+
+    wl = W.plain_h2_ca()
+    out["plain_fp64"] = time_steps(Q, wl, tuned(wl, Q.make_integ(**wl.integ, persistent=True)),
+                                   5, 3, dev)
+    wl = W.sweep_h2_ca()
+    wl.integ = dict(W.INTEG_FP32)
+    wl.name += "_fp32"
+    out["sweep_fp32"] = time_steps(
+        Q, wl, Q.make_integ(**wl.integ, persistent=True, precision=32), 5, 3, dev)
+    del wl
+    torch.cuda.empty_cache()
+    wl = W.mixed_ca_h()
+    out["mixed_fp64"] = time_steps(Q, wl, tuned(wl, Q.make_integ(**wl.integ, persistent=True)),
+                                   1, 1, dev)
+    del wl
+    torch.cuda.empty_cache()
+    learned = learned_study(argparse.Namespace(train_lanes=1_000_000, is_lanes=200_000,
+                                               train_precision=32, warmup=1))
+    out["learned"] = {k: learned[k] for k in ("metric", "value", "unit", "config", "training",
+                                               "amortised", "clocks")}
+    out["learned"]["per_energy_fom_gain"] = [r["fom_gain"] for r in learned["per_energy"]]
+    return out
+
+
 def run_learned(args):
+    print(json.dumps(learned_study(args)), flush=True)
+    return 0
+
+
+def learned_study(args):
     """The learned-proposal study: train the outcome network on trajectories
     of the LJ(12,6) Ca-H system drawn like the mixed study, then estimate
     sigma_R = sigma(AC+B) + sigma(BC+A) at E = 0.05, 0.10, 0.15 hartree for
@@ -534,9 +637,13 @@ def run_learned(args):
     from paper_2304_02731_gb300 import workloads as W
     torch.cuda.set_device(0)
     spec_sys = W.SYS_H2_CA_LJ12
+    # warm-up: load the generation and training kernels once (a few lanes,
+    # a few steps), so that the timed network cost is the steady-state one
+    xw, cw, _ = L.generate(spec_sys, 4096, seed=7, precision=args.train_precision)
+    L.train(Q.MLP(seed=2), xw, cw, epochs=1, batch=1024, lr=2e-3)
+    torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
-    torch.cuda.synchronize()
     t0 = time.perf_counter()
     x, cls, host = L.generate(spec_sys, args.train_lanes, seed=101,
                               precision=args.train_precision)
@@ -593,8 +700,7 @@ def run_learned(args):
                                   "to the run's estimates"},
             "clocks": clock_info,
             "per_energy": rows}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def main():

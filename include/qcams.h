@@ -383,7 +383,8 @@ int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys, const qcams_
  * events.  The sample's state is restored afterwards.  results (host, room
  * for QCAMS_TUNE_MAX_VARIANTS entries) receives one entry per variant,
  * *n_results their number, and *best a copy of *integ with the fastest
- * shape and persistent = 1.  Synchronous; allocates a temporary copy of the
+ * shape and persistent = 1; shapes within 2 % of the fastest count as a tie,
+ * which goes to the smallest block (then the fewest blocks per SM).  Synchronous; allocates a temporary copy of the
  * sample state (~121 bytes per lane) with cudaMallocAsync.
  */
 #define QCAMS_TUNE_MAX_VARIANTS 16

@@ -1034,6 +1034,20 @@ int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* in
     }
     *n_results = v + 1;
   }
+  // Shapes within 2 % of the fastest on the sample are a tie (the sample's
+  // attempt cap evens out trajectory lengths): the tie goes to the smallest
+  // block, which schedules the full workload's uneven lanes at the finest
+  // grain (measured on the full sweep: 64 x 1 at 22.25 s against 256 x 1 at
+  // 23.5 s, equal on the sample).
+  if (e == cudaSuccess && best_v >= 0) {
+    for (int v = 0; v < *n_results; ++v) {
+      const qcams_tune_result& r = results[v];
+      const qcams_tune_result& b = results[best_v];
+      if (r.lane_steps_per_s >= 0.98 * best_rate &&
+          (r.block < b.block || (r.block == b.block && r.blocks_per_sm < b.blocks_per_sm)))
+        best_v = v;
+    }
+  }
   cudaError_t e2 = copy_all(false);
   cudaFreeAsync(save, st);
   if (e == cudaSuccess) e = e2;
