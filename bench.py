@@ -101,6 +101,11 @@ def parse():
                     help="learned: trajectories generated to train the network")
     ap.add_argument("--is-lanes", type=int, default=200_000,
                     help="learned: trajectories per estimate (proposal and uniform)")
+    ap.add_argument("--train-epochs", type=int, default=24,
+                    help="learned: passes over the training lanes")
+    ap.add_argument("--train-batch", type=int, default=8192,
+                    help="learned: minibatch rows per Adam step")
+    ap.add_argument("--train-lr", type=float, default=2e-3, help="learned: Adam learning rate")
     ap.add_argument("--train-precision", type=int, default=32, choices=[64, 32],
                     help="learned: integrator of the training trajectories (the estimates "
                          "are always FP64)")
@@ -599,7 +604,8 @@ def run_extras(args, dev):
     del wl
     torch.cuda.empty_cache()
     learned = learned_study(argparse.Namespace(train_lanes=1_000_000, is_lanes=200_000,
-                                               train_precision=32, warmup=1))
+                                               train_precision=32, warmup=1, train_epochs=24,
+                                               train_batch=8192, train_lr=2e-3))
     out["learned"] = {k: learned[k] for k in ("metric", "value", "unit", "config", "training",
                                                "amortised", "clocks")}
     out["learned"]["per_energy_fom_gain"] = [r["fom_gain"] for r in learned["per_energy"]]
@@ -651,7 +657,8 @@ def learned_study(args):
     t_gen = time.perf_counter() - t0
     mlp = Q.MLP(seed=1)
     t0 = time.perf_counter()
-    losses = L.train(mlp, x, cls, epochs=24, batch=8192, lr=2e-3)
+    losses = L.train(mlp, x, cls, epochs=args.train_epochs, batch=args.train_batch,
+                     lr=args.train_lr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     cost = t_gen + t_train
@@ -687,7 +694,8 @@ def learned_study(args):
                        "is_lanes_per_estimate": args.is_lanes,
                        "state": {"v": v, "j": j, "train_reactive_fraction": frac}},
             "training": {"generate_s": t_gen, "train_s": t_train, "loss_first": losses[0],
-                         "loss_last": losses[-1], "epochs": len(losses)},
+                         "loss_last": losses[-1], "epochs": len(losses),
+                         "batch": args.train_batch, "lr": args.train_lr},
             "amortised": {"network_cost_s": cost,
                           "fom_gain_amortised_over_run": float(np.exp(np.mean(np.log(amort)))),
                           "estimates_in_run": len(energies),
