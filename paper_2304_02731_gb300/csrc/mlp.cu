@@ -10,9 +10,10 @@
 // register layout of the A operand of a 16x16 slice, so a layer's SiLU output
 // is fed to the next layer's products without touching shared memory.  The
 // backward pass reuses the same fragments: dA = dZ W uses transposed weights
-// staged in shared memory; dW = dZ^T A takes dZ^T and A^T from per-warp
-// shared tiles written during the pass.  Per-CTA FP32 gradient accumulators
-// in shared memory are flushed to global memory once per CTA.
+// staged in shared memory.  Training leaves each block round's transposed
+// activations and errors in shared tiles; the weight gradients dW = dZ^T A
+// are then block GEMMs over the round's samples (K = 128), accumulated in
+// registers and added to the global gradient once per round.
 //
 // The network is ~9k multiply-adds per sample: negligible next to the
 // trajectory integration, so a warp-level mma kernel is enough here.
@@ -32,6 +33,8 @@ constexpr int IN = 8, H = 64, OUT = 4, NP = QCAMS_MLP_NPARAMS;
 constexpr int OW1 = 0, OB1 = OW1 + H * IN, OW2 = OB1 + H, OB2 = OW2 + H * H, OW3 = OB2 + H,
               OB3 = OW3 + H * H, OW4 = OB3 + H, OB4 = OW4 + OUT * H;
 static_assert(OB4 + OUT == NP, "parameter layout");
+static_assert(OW1 % 2 == 0 && OW2 % 2 == 0 && OW3 % 2 == 0 && OW4 % 2 == 0 && IN % 2 == 0,
+              "weight-gradient pairs are 8-byte aligned");
 constexpr int WARPS = 4, THREADS = WARPS * 32;
 constexpr double kPi = 3.14159265358979323846;
 
@@ -55,33 +58,36 @@ struct WeightsSmem {
   __nv_bfloat16 w4t[H][16 + PK];
   float b1[H], b2[H], b3[H], b4[8];
 };
-struct WarpSmem {
-  float z[3][32][32];               // pre-activations of layers 1-3, fragment order [i][lane]
-  __nv_bfloat16 xt[16][16 + PK];    // X^T  [feature (padded)][sample]
-  __nv_bfloat16 at[3][H][16 + PK];  // A1^T, A2^T, A3^T [unit][sample]
-  __nv_bfloat16 dzt[H][16 + PK];    // dZ^T [unit][sample]
+// Training works in rounds of RS = 128 samples per block (4 warps x 2 chunks
+// of 16).  Each chunk's forward and backward pass leave, in block-wide
+// shared tiles, the transposed inputs, activations and back-propagated
+// errors of its 16 samples (BF16, [unit][sample]); after the round each
+// warp forms 16 rows of every weight gradient dW = dZ^T A as an MMA product
+// over the round's 128 samples, accumulated in registers and added to the
+// global gradient once.  Rows are padded by 8 elements: a fragment load
+// touches rows g = 0..7 at words q + const, and the 272-byte row stride (68
+// words) puts them on 32 distinct banks.
+constexpr int RS = 2 * 16 * WARPS;   // samples per block round
+constexpr int LDT = RS + PK;         // row stride of the sample tiles (BF16 elements)
+struct BlockTiles {
+  __nv_bfloat16 xt[16][LDT];         // X^T  [feature (padded to 16)][sample]
+  __nv_bfloat16 at[3][H][LDT];       // A1^T, A2^T, A3^T [unit][sample]
+  __nv_bfloat16 dzt[3][H][LDT];      // dZ1^T, dZ2^T, dZ3^T [unit][sample]
+  __nv_bfloat16 dz4t[16][LDT];       // dZ4^T [output (padded to 16)][sample]
 };
-// The block's gradient accumulator in shared memory: the parameter layout
-// with the rows of W2, W3 and W4 padded from 64 to 68 floats, so that the
-// eight rows an MMA fragment adds into fall on different banks (2-way
-// instead of 8-way conflicts of the shared atomics).
-constexpr int GLD = 68;
-constexpr int SW1 = 0, SB1 = SW1 + H * IN, SW2 = SB1 + H, SB2 = SW2 + H * GLD, SW3 = SB2 + H,
-              SB3 = SW3 + H * GLD, SW4 = SB3 + H, SB4 = SW4 + OUT * GLD, NPS = SB4 + OUT;
-// Position in the padded accumulator of parameter i (linear layout).
-__device__ __forceinline__ int padded(int i) {
-  if (i >= OW2 && i < OB2) return SW2 + ((i - OW2) >> 6) * GLD + ((i - OW2) & 63);
-  if (i >= OW3 && i < OB3) return SW3 + ((i - OW3) >> 6) * GLD + ((i - OW3) & 63);
-  if (i >= OW4 && i < OB4) return SW4 + ((i - OW4) >> 6) * GLD + ((i - OW4) & 63);
-  if (i < OW2) return i;                     // W1, b1 (no padding before them)
-  if (i < OW3) return i - OB2 + SB2;         // b2
-  if (i < OW4) return i - OB3 + SB3;         // b3
-  return i - OB4 + SB4;                      // b4
-}
+// Pre-activations of the warp's current chunk (layers 1-3), fragment order
+// [i][lane], for SiLU' in the backward pass.
+struct WarpZ {
+  float z[3][32][32];
+};
+// Bias gradients of the block (b1, b2, b3, b4), FP32 sums of the FP32 dZ
+// fragments.
+constexpr int GB1 = 0, GB2 = H, GB3 = 2 * H, GB4 = 3 * H, NGB = 3 * H + OUT;
 struct TrainSmem {
   WeightsSmem w;
-  float grad[NPS];
-  WarpSmem warp[WARPS];
+  float gb[NGB];
+  BlockTiles t;
+  WarpZ wz[WARPS];
 };
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
@@ -172,12 +178,13 @@ __device__ __forceinline__ void features(const float* x, const int64_t* idx, int
 
 // Forward pass of 16 samples (rows base .. base+15) by one warp.  Returns the
 // logits fragment (rows g and g+8, columns 2q, 2q+1 of the padded 16x8 tile).
-// With TRAIN, pre-activations and transposed activations are kept in the
-// warp's shared tiles for the backward pass.
+// With TRAIN, pre-activations go to the warp's z tiles and the transposed
+// inputs and activations to the block tiles T, at sample columns col ..
+// col + 15, for the backward pass.
 template <bool TRAIN>
-__device__ void forward16(const WeightsSmem& W, WarpSmem* ws, const float* x, const int64_t* idx,
-                          int64_t n, int64_t base, const CellGrid* grid, const Std& sd,
-                          float* logit) {
+__device__ void forward16(const WeightsSmem& W, WarpZ* wz, BlockTiles* T, int col, const float* x,
+                          const int64_t* idx, int64_t n, int64_t base, const CellGrid* grid,
+                          const Std& sd, float* logit) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   float f0[IN], f1[IN];
   features(x, idx, n, base + g, grid, f0);
@@ -194,12 +201,10 @@ __device__ void forward16(const WeightsSmem& W, WarpSmem* ws, const float* x, co
   a[0][2] = 0u;
   a[0][3] = 0u;
   if (TRAIN) {
-    ws->xt[2 * q][g] = __float2bfloat16(f0[2 * q]);
-    ws->xt[2 * q + 1][g] = __float2bfloat16(f0[2 * q + 1]);
-    ws->xt[2 * q][g + 8] = __float2bfloat16(f1[2 * q]);
-    ws->xt[2 * q + 1][g + 8] = __float2bfloat16(f1[2 * q + 1]);
-    ws->xt[8 + 2 * q][g] = ws->xt[8 + 2 * q + 1][g] = __float2bfloat16(0.0f);
-    ws->xt[8 + 2 * q][g + 8] = ws->xt[8 + 2 * q + 1][g + 8] = __float2bfloat16(0.0f);
+    T->xt[2 * q][col + g] = __float2bfloat16(f0[2 * q]);
+    T->xt[2 * q + 1][col + g] = __float2bfloat16(f0[2 * q + 1]);
+    T->xt[2 * q][col + g + 8] = __float2bfloat16(f1[2 * q]);
+    T->xt[2 * q + 1][col + g + 8] = __float2bfloat16(f1[2 * q + 1]);
   }
   float c[8][4];
   for (int layer = 0; layer < 3; ++layer) {
@@ -220,7 +225,7 @@ __device__ void forward16(const WeightsSmem& W, WarpSmem* ws, const float* x, co
 #pragma unroll
       for (int t = 0; t < 8; ++t)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) ws->z[layer][4 * t + e][lane] = c[t][e];
+        for (int e = 0; e < 4; ++e) wz->z[layer][4 * t + e][lane] = c[t][e];
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -234,14 +239,15 @@ __device__ void forward16(const WeightsSmem& W, WarpSmem* ws, const float* x, co
       a[s][3] = pack2(w2, w3);
       if (TRAIN) {
         const int c0 = 16 * s + 2 * q, c1 = 16 * s + 8 + 2 * q;
-        ws->at[layer][c0][g] = __float2bfloat16(v0);
-        ws->at[layer][c0 + 1][g] = __float2bfloat16(v1);
-        ws->at[layer][c0][g + 8] = __float2bfloat16(v2);
-        ws->at[layer][c0 + 1][g + 8] = __float2bfloat16(v3);
-        ws->at[layer][c1][g] = __float2bfloat16(w0);
-        ws->at[layer][c1 + 1][g] = __float2bfloat16(w1);
-        ws->at[layer][c1][g + 8] = __float2bfloat16(w2);
-        ws->at[layer][c1 + 1][g + 8] = __float2bfloat16(w3);
+        __nv_bfloat16 (*at)[LDT] = T->at[layer];
+        at[c0][col + g] = __float2bfloat16(v0);
+        at[c0 + 1][col + g] = __float2bfloat16(v1);
+        at[c0][col + g + 8] = __float2bfloat16(v2);
+        at[c0 + 1][col + g + 8] = __float2bfloat16(v3);
+        at[c1][col + g] = __float2bfloat16(w0);
+        at[c1 + 1][col + g] = __float2bfloat16(w1);
+        at[c1][col + g + 8] = __float2bfloat16(w2);
+        at[c1 + 1][col + g + 8] = __float2bfloat16(w3);
       }
     }
   }
@@ -266,42 +272,57 @@ __device__ __forceinline__ void softmax_pair(float z0, float z1, float* p0, floa
   *p1 = e1 / s;
 }
 
-// dW (+)= dZ^T A for one layer: M = n_out (16-row tiles), K = 16 samples,
-// N = n_in (8-column tiles), into the CTA gradient accumulator (row stride ld).
-__device__ void accumulate_dw(const WarpSmem* ws, const __nv_bfloat16 (*aT)[16 + PK], int m_tiles,
-                              int n_tiles, int n_out_valid, int n_in, int ld, float* gW) {
+// One warp's 16 rows m0 .. m0+15 of dW = dZ^T A over the round's RS samples,
+// for the n_tiles 8-column tiles from column n0: A operand from dZ^T (rows
+// = output units, samples contiguous), B operand from A^T (rows = input
+// units, samples contiguous: the col layout of B), FP32 accumulation in
+// registers; added once to the global gradient gW (row-major, n_in columns)
+// for rows < n_out and columns < n_in.
+__device__ void block_dw(const __nv_bfloat16 (*dzt)[LDT], const __nv_bfloat16 (*at)[LDT], int m0,
+                         int n0, int n_tiles, int n_out, int n_in, float* gW) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  for (int mt = 0; mt < m_tiles; ++mt) {
+  float d[8][4];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) d[t][0] = d[t][1] = d[t][2] = d[t][3] = 0.0f;
+#pragma unroll 2
+  for (int ks = 0; ks < RS / 16; ++ks) {
     uint32_t a[4];
-    a[0] = ld2(&ws->dzt[16 * mt + g][2 * q]);
-    a[1] = ld2(&ws->dzt[16 * mt + g + 8][2 * q]);
-    a[2] = ld2(&ws->dzt[16 * mt + g][8 + 2 * q]);
-    a[3] = ld2(&ws->dzt[16 * mt + g + 8][8 + 2 * q]);
-    for (int nt = 0; nt < n_tiles; ++nt) {
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
-      mma(d, a, ld2(&aT[8 * nt + g][2 * q]), ld2(&aT[8 * nt + g][8 + 2 * q]));
-      const int r0 = 16 * mt + g, r1 = r0 + 8, col = 8 * nt + 2 * q;
-      if (r0 < n_out_valid && col < n_in) {
-        atomicAdd(&gW[r0 * ld + col], d[0]);
-        atomicAdd(&gW[r0 * ld + col + 1], d[1]);
+    a[0] = ld2(&dzt[m0 + g][16 * ks + 2 * q]);
+    a[1] = ld2(&dzt[m0 + g + 8][16 * ks + 2 * q]);
+    a[2] = ld2(&dzt[m0 + g][16 * ks + 8 + 2 * q]);
+    a[3] = ld2(&dzt[m0 + g + 8][16 * ks + 8 + 2 * q]);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      if (t < n_tiles) {
+        const __nv_bfloat16* br = &at[n0 + 8 * t + g][16 * ks];
+        mma(d[t], a, ld2(br + 2 * q), ld2(br + 8 + 2 * q));
       }
-      if (r1 < n_out_valid && col < n_in) {
-        atomicAdd(&gW[r1 * ld + col], d[2]);
-        atomicAdd(&gW[r1 * ld + col + 1], d[3]);
-      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (t >= n_tiles) continue;
+    const int r0 = m0 + g, r1 = r0 + 8, c = n0 + 8 * t + 2 * q;
+    // c and n_in are even and the parameter offsets are even: 8-byte
+    // aligned pairs (vector atomics, sm_90 and later)
+    if (c < n_in) {
+      if (r0 < n_out) atomicAdd(reinterpret_cast<float2*>(&gW[r0 * n_in + c]), make_float2(d[t][0], d[t][1]));
+      if (r1 < n_out) atomicAdd(reinterpret_cast<float2*>(&gW[r1 * n_in + c]), make_float2(d[t][2], d[t][3]));
     }
   }
 }
 
-// Write dZ (fragment layout, 16 samples x 8 t-tiles) transposed into dzt.
-__device__ __forceinline__ void store_dzt(WarpSmem* ws, const float (*dz)[4], int tiles) {
+// Write dZ (fragment layout: 16 samples x `tiles` 8-unit tiles) transposed
+// into the block tile dst at sample columns col .. col + 15.
+__device__ __forceinline__ void store_dz(__nv_bfloat16 (*dst)[LDT], int col, const float (*dz)[4],
+                                         int tiles) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
   for (int t = 0; t < tiles; ++t) {
     const int c0 = 8 * t + 2 * q;
-    ws->dzt[c0][g] = __float2bfloat16(dz[t][0]);
-    ws->dzt[c0 + 1][g] = __float2bfloat16(dz[t][1]);
-    ws->dzt[c0][g + 8] = __float2bfloat16(dz[t][2]);
-    ws->dzt[c0 + 1][g + 8] = __float2bfloat16(dz[t][3]);
+    dst[c0][col + g] = __float2bfloat16(dz[t][0]);
+    dst[c0 + 1][col + g] = __float2bfloat16(dz[t][1]);
+    dst[c0][col + g + 8] = __float2bfloat16(dz[t][2]);
+    dst[c0 + 1][col + g + 8] = __float2bfloat16(dz[t][3]);
   }
 }
 
@@ -325,7 +346,12 @@ __device__ __forceinline__ void accumulate_db(const float (*dz)[4], int tiles, i
 }
 
 // Gradient of the mean cross-entropy over n rows; with idx, row r of the
-// minibatch is sample idx[r] of (x, label).
+// minibatch is sample idx[r] of (x, label).  Block rounds of RS samples: each
+// warp carries its chunks of 16 through the forward and backward passes
+// (activations and errors to the block tiles, bias gradients to shared FP32
+// sums), then the four weight gradients of the round are formed as block
+// GEMMs (warp w: rows 16w .. 16w+15 of dW1..dW3, columns 16w .. 16w+15 of
+// dW4) and added to the global gradient.
 __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, const float* pf,
                                                       Std sd, const float* x,
                                                       const uint8_t* label, const int64_t* idx,
@@ -333,97 +359,98 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   load_weights(S.w, pb, pf);
-  for (int i = threadIdx.x; i < NPS; i += blockDim.x) S.grad[i] = 0.0f;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
-  WarpSmem* ws = &S.warp[warp];
-  for (int i = lane; i < H * (16 + PK); i += 32) (&ws->dzt[0][0])[i] = __float2bfloat16(0.0f);
+  for (int i = threadIdx.x; i < NGB; i += blockDim.x) S.gb[i] = 0.0f;
+  // padding rows of the X^T and dZ4^T tiles (never written by the passes)
+  const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+  for (int i = threadIdx.x; i < (16 - IN) * LDT; i += blockDim.x) S.t.xt[IN + i / LDT][i % LDT] = zero;
+  for (int i = threadIdx.x; i < (16 - 8) * LDT; i += blockDim.x) S.t.dz4t[8 + i / LDT][i % LDT] = zero;
   __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  WarpZ* wz = &S.wz[warp];
   const float inv_n = 1.0f / (float)n;
   float loss_acc = 0.0f;
-  const int64_t chunks = (n + 15) / 16;
-  for (int64_t ch = (int64_t)blockIdx.x * WARPS + warp; ch < chunks;
-       ch += (int64_t)gridDim.x * WARPS) {
-    const int64_t base = ch * 16;
-    float lg[4];
-    forward16<true>(S.w, ws, x, idx, n, base, nullptr, sd, lg);
-    // softmax cross-entropy and dZ4 = (p - onehot) / n
-    float dz4[1][4] = {{0.f, 0.f, 0.f, 0.f}};
-    float p[4];
-    softmax_pair(lg[0], lg[1], &p[0], &p[1]);
-    softmax_pair(lg[2], lg[3], &p[2], &p[3]);
-    if (q < 2) {
-      const int64_t r0 = base + g, r1 = base + g + 8;
-      int l0 = r0 < n ? (int)label[idx ? idx[r0] : r0] : -1;
-      int l1 = r1 < n ? (int)label[idx ? idx[r1] : r1] : -1;
-      if (l0 >= OUT) l0 = -1;   // AMBIG / FAIL lanes carry no target
-      if (l1 >= OUT) l1 = -1;
-      for (int e = 0; e < 2; ++e) {
-        const int col = 2 * q + e;
-        if (l0 >= 0) {
-          dz4[0][e] = (p[e] - (col == l0 ? 1.0f : 0.0f)) * inv_n;
-          if (col == l0) loss_acc -= __logf(fmaxf(p[e], 1e-30f)) * inv_n;
+  const int64_t rounds = (n + RS - 1) / RS;
+  for (int64_t rnd = blockIdx.x; rnd < rounds; rnd += gridDim.x) {
+    for (int c = 0; c < RS / (16 * WARPS); ++c) {
+      const int col = 16 * (WARPS * c + warp);
+      const int64_t base = rnd * RS + col;
+      float lg[4];
+      forward16<true>(S.w, wz, &S.t, col, x, idx, n, base, nullptr, sd, lg);
+      // softmax cross-entropy and dZ4 = (p - onehot) / n; rows past n and
+      // rows without a target have dZ4 = 0 and so add nothing below
+      float dz4[1][4] = {{0.f, 0.f, 0.f, 0.f}};
+      float p[4];
+      softmax_pair(lg[0], lg[1], &p[0], &p[1]);
+      softmax_pair(lg[2], lg[3], &p[2], &p[3]);
+      if (q < 2) {
+        const int64_t r0 = base + g, r1 = base + g + 8;
+        int l0 = r0 < n ? (int)label[idx ? idx[r0] : r0] : -1;
+        int l1 = r1 < n ? (int)label[idx ? idx[r1] : r1] : -1;
+        if (l0 >= OUT) l0 = -1;   // AMBIG / FAIL lanes carry no target
+        if (l1 >= OUT) l1 = -1;
+        for (int e = 0; e < 2; ++e) {
+          const int k = 2 * q + e;
+          if (l0 >= 0) {
+            dz4[0][e] = (p[e] - (k == l0 ? 1.0f : 0.0f)) * inv_n;
+            if (k == l0) loss_acc -= __logf(fmaxf(p[e], 1e-30f)) * inv_n;
+          }
+          if (l1 >= 0) {
+            dz4[0][2 + e] = (p[2 + e] - (k == l1 ? 1.0f : 0.0f)) * inv_n;
+            if (k == l1) loss_acc -= __logf(fmaxf(p[2 + e], 1e-30f)) * inv_n;
+          }
         }
-        if (l1 >= 0) {
-          dz4[0][2 + e] = (p[2 + e] - (col == l1 ? 1.0f : 0.0f)) * inv_n;
-          if (col == l1) loss_acc -= __logf(fmaxf(p[2 + e], 1e-30f)) * inv_n;
+      }
+      store_dz(S.t.dz4t, col, dz4, 1);
+      accumulate_db(dz4, 1, OUT, &S.gb[GB4]);
+      // dA3 = dZ4 W4: A operand from the dZ4 fragment (K padded 8 -> 16)
+      uint32_t a[4][4];
+      a[0][0] = pack2(dz4[0][0], dz4[0][1]);
+      a[0][1] = pack2(dz4[0][2], dz4[0][3]);
+      a[0][2] = 0u;
+      a[0][3] = 0u;
+      float dz[8][4];
+      for (int layer = 2; layer >= 0; --layer) {
+        const int ks = layer == 2 ? 1 : 4;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          dz[t][0] = dz[t][1] = dz[t][2] = dz[t][3] = 0.0f;
+          for (int s = 0; s < ks; ++s) {
+            const __nv_bfloat16* wr = layer == 2 ? &S.w.w4t[8 * t + g][0]
+                                      : layer == 1 ? &S.w.w3t[8 * t + g][16 * s]
+                                                   : &S.w.w2t[8 * t + g][16 * s];
+            mma(dz[t], a[s], ld2(wr + 2 * q), ld2(wr + 8 + 2 * q));
+          }
+          // dZ = dA * SiLU'(Z)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) dz[t][e] *= dsilu(wz->z[layer][4 * t + e][lane]);
+        }
+        store_dz(S.t.dzt[layer], col, dz, 8);
+        accumulate_db(dz, 8, H, &S.gb[GB1 + H * layer]);
+        if (layer > 0) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            a[s][0] = pack2(dz[2 * s][0], dz[2 * s][1]);
+            a[s][1] = pack2(dz[2 * s][2], dz[2 * s][3]);
+            a[s][2] = pack2(dz[2 * s + 1][0], dz[2 * s + 1][1]);
+            a[s][3] = pack2(dz[2 * s + 1][2], dz[2 * s + 1][3]);
+          }
         }
       }
     }
-    // output layer gradients
-    __syncwarp();
-    store_dzt(ws, dz4, 1);
-    __syncwarp();
-    accumulate_dw(ws, ws->at[2], 1, 8, OUT, H, GLD, &S.grad[SW4]);
-    accumulate_db(dz4, 1, OUT, &S.grad[SB4]);
-    // dA3 = dZ4 W4: A operand from the dZ4 fragment (K padded 8 -> 16)
-    uint32_t a[4][4];
-    a[0][0] = pack2(dz4[0][0], dz4[0][1]);
-    a[0][1] = pack2(dz4[0][2], dz4[0][3]);
-    a[0][2] = 0u;
-    a[0][3] = 0u;
-    float dz[8][4];
-    for (int layer = 2; layer >= 0; --layer) {
-      const int ks = layer == 2 ? 1 : 4;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        dz[t][0] = dz[t][1] = dz[t][2] = dz[t][3] = 0.0f;
-        for (int s = 0; s < ks; ++s) {
-          const __nv_bfloat16* wr = layer == 2 ? &S.w.w4t[8 * t + g][0]
-                                    : layer == 1 ? &S.w.w3t[8 * t + g][16 * s]
-                                                 : &S.w.w2t[8 * t + g][16 * s];
-          mma(dz[t], a[s], ld2(wr + 2 * q), ld2(wr + 8 + 2 * q));
-        }
-        // dZ = dA * SiLU'(Z)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) dz[t][e] *= dsilu(ws->z[layer][4 * t + e][lane]);
-      }
-      __syncwarp();
-      store_dzt(ws, dz, 8);
-      __syncwarp();
-      float* gW = layer == 2 ? &S.grad[SW3] : layer == 1 ? &S.grad[SW2] : &S.grad[SW1];
-      float* gb = layer == 2 ? &S.grad[SB3] : layer == 1 ? &S.grad[SB2] : &S.grad[SB1];
-      if (layer > 0) accumulate_dw(ws, ws->at[layer - 1], 4, 8, H, H, GLD, gW);
-      else accumulate_dw(ws, ws->xt, 4, 1, H, IN, IN, gW);
-      accumulate_db(dz, 8, H, gb);
-      if (layer > 0) {
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          a[s][0] = pack2(dz[2 * s][0], dz[2 * s][1]);
-          a[s][1] = pack2(dz[2 * s][2], dz[2 * s][3]);
-          a[s][2] = pack2(dz[2 * s + 1][0], dz[2 * s + 1][1]);
-          a[s][3] = pack2(dz[2 * s + 1][2], dz[2 * s + 1][3]);
-        }
-      }
-      __syncwarp();
-    }
+    __syncthreads();   // the round's tiles are complete
+    const int m0 = 16 * warp;
+    block_dw(S.t.dzt[0], S.t.xt, m0, 0, 1, H, IN, grad + OW1);
+    block_dw(S.t.dzt[1], S.t.at[0], m0, 0, 8, H, H, grad + OW2);
+    block_dw(S.t.dzt[2], S.t.at[1], m0, 0, 8, H, H, grad + OW3);
+    block_dw(S.t.dz4t, S.t.at[2], 0, m0, 2, OUT, H, grad + OW4);
+    __syncthreads();   // tiles are rewritten by the next round
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, o);
   if (lane == 0 && loss) atomicAdd(loss, loss_acc);
-  __syncthreads();
-  for (int i = threadIdx.x; i < NP; i += blockDim.x) {
-    const float v = S.grad[padded(i)];
-    if (v != 0.0f) atomicAdd(&grad[i], v);
+  for (int i = threadIdx.x; i < NGB; i += blockDim.x) {
+    const int k = i < 3 * H ? (i / H == 0 ? OB1 : i / H == 1 ? OB2 : OB3) + i % H : OB4 + (i - 3 * H);
+    if (S.gb[i] != 0.0f) atomicAdd(&grad[k], S.gb[i]);
   }
 }
 
@@ -441,7 +468,8 @@ __global__ void __launch_bounds__(THREADS) k_mlp_infer(const __nv_bfloat16* pb, 
        ch += (int64_t)gridDim.x * WARPS) {
     const int64_t base = ch * 16;
     float lg[4], p[4];
-    forward16<false>(W, nullptr, x, nullptr, n, base, use_grid ? &grid : nullptr, sd, lg);
+    forward16<false>(W, nullptr, nullptr, 0, x, nullptr, n, base, use_grid ? &grid : nullptr, sd,
+                     lg);
     softmax_pair(lg[0], lg[1], &p[0], &p[1]);
     softmax_pair(lg[2], lg[3], &p[2], &p[3]);
     const int64_t r0 = base + g, r1 = base + g + 8;
@@ -693,12 +721,12 @@ int launch_grad(const qcams_mlp* m, const float* x, const uint8_t* label, const 
   const size_t smem = sizeof(TrainSmem);
   e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return QCAMS_E_CUDA;
-  const int64_t chunks = (n + 15) / 16;
-  // ~2 chunks of 16 samples per warp, at most one block per SM (the block
-  // holds the weights and its gradient in 160 KB of shared memory): a batch
-  // of 8,192 samples spreads over 64 SMs, and each block's one flush of its
-  // gradient (9,156 global atomics) is amortised over 128 samples
-  int64_t grid = (chunks + WARPS * 2 - 1) / (WARPS * 2);
+  // one block round of RS = 128 samples per block, at most one block per SM
+  // (the weights, the round's tiles and the warps' pre-activations take
+  // 203 KB of shared memory): a batch of 8,192 samples runs as 64 blocks of
+  // one round each, and each weight gradient element gets one vector atomic
+  // per block
+  int64_t grid = (n + RS - 1) / RS;
   if (grid > sm_count()) grid = sm_count();
   if (grid < 1) grid = 1;
   k_mlp_grad<<<(unsigned)grid, THREADS, smem, st>>>(
