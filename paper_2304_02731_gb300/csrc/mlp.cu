@@ -48,7 +48,7 @@ struct Std {
 // a fragment load touches rows g = 0..7 at words 2q / 2 + const, and the
 // 16-byte row skew puts the 8 rows x 4 words on 32 distinct banks.
 constexpr int PK = 8;   // row padding (BF16 elements)
-struct WeightsSmem {
+struct alignas(16) WeightsSmem {   // 16-byte row-segment stores
   __nv_bfloat16 w1[H][16 + PK];
   __nv_bfloat16 w2[H][H + PK];
   __nv_bfloat16 w3[H][H + PK];
@@ -58,35 +58,37 @@ struct WeightsSmem {
   __nv_bfloat16 w4t[H][16 + PK];
   float b1[H], b2[H], b3[H], b4[8];
 };
-// Training works in rounds of RS = 128 samples per block (4 warps x 2 chunks
-// of 16).  Each chunk's forward and backward pass leave, in block-wide
-// shared tiles, the transposed inputs, activations and back-propagated
-// errors of its 16 samples (BF16, [unit][sample]); after the round each
-// warp forms 16 rows of every weight gradient dW = dZ^T A as an MMA product
-// over the round's 128 samples, accumulated in registers and added to the
-// global gradient once.  Rows are padded by 8 elements: a fragment load
-// touches rows g = 0..7 at words q + const, and the 272-byte row stride (68
-// words) puts them on 32 distinct banks.
-constexpr int RS = 2 * 16 * WARPS;   // samples per block round
-constexpr int LDT = RS + PK;         // row stride of the sample tiles (BF16 elements)
+// Training works in block rounds of RS = 64 CPW samples (4 warps x CPW
+// chunks of 16).  Each chunk's forward and backward pass leave, in
+// block-wide shared tiles, the transposed inputs, activations and
+// back-propagated errors of its 16 samples (BF16, [unit][sample]); after the
+// round each warp forms 16 rows of every weight gradient dW = dZ^T A as an
+// MMA product over the round's samples, accumulated in registers and added
+// to the global gradient once.  Rows are padded by 8 elements: a fragment
+// load touches rows g = 0..7 at words q + const, and a row stride of
+// 32 CPW + 4 words puts them on 32 distinct banks.
+template <int CPW>
 struct BlockTiles {
+  static constexpr int RS = 16 * WARPS * CPW;   // samples per block round
+  static constexpr int LDT = RS + PK;           // row stride (BF16 elements)
   __nv_bfloat16 xt[16][LDT];         // X^T  [feature (padded to 16)][sample]
   __nv_bfloat16 at[3][H][LDT];       // A1^T, A2^T, A3^T [unit][sample]
   __nv_bfloat16 dzt[3][H][LDT];      // dZ1^T, dZ2^T, dZ3^T [unit][sample]
   __nv_bfloat16 dz4t[16][LDT];       // dZ4^T [output (padded to 16)][sample]
 };
-// Pre-activations of the warp's current chunk (layers 1-3), fragment order
-// [i][lane], for SiLU' in the backward pass.
+// SiLU'(Z) of the warp's current chunk (layers 1-3), fragment order
+// [i][lane], computed in the forward pass for the backward pass.
 struct WarpZ {
-  float z[3][32][32];
+  float ds[3][32][32];
 };
 // Bias gradients of the block (b1, b2, b3, b4), FP32 sums of the FP32 dZ
 // fragments.
-constexpr int GB1 = 0, GB2 = H, GB3 = 2 * H, GB4 = 3 * H, NGB = 3 * H + OUT;
+constexpr int GB1 = 0, NGB = 3 * H + OUT;
+template <int CPW>
 struct TrainSmem {
   WeightsSmem w;
   float gb[NGB];
-  BlockTiles t;
+  BlockTiles<CPW> t;
   WarpZ wz[WARPS];
 };
 
@@ -107,33 +109,92 @@ __device__ __forceinline__ void mma(float* d, const uint32_t* a, uint32_t b0, ui
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + __expf(-z)); }
-__device__ __forceinline__ float silu(float z) { return z * sigm(z); }
-__device__ __forceinline__ float dsilu(float z) {
-  const float s = sigm(z);
-  return s * (1.0f + z * (1.0f - s));
+// Logistic function: __expf and the fast divide (a few ulp; the products it
+// feeds are rounded to BF16).  For z below about -87 the quotient is 0.
+__device__ __forceinline__ float sigm(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+
+__device__ __forceinline__ __nv_bfloat16 bf_lo(uint32_t w) {
+  return __ushort_as_bfloat16((unsigned short)(w & 0xffffu));
+}
+__device__ __forceinline__ __nv_bfloat16 bf_hi(uint32_t w) {
+  return __ushort_as_bfloat16((unsigned short)(w >> 16));
 }
 
+// Weights to shared memory (blockDim.x == THREADS).  With p 16-byte aligned
+// every matrix starts on a 16-byte boundary: each thread issues all of its
+// 16-byte loads of 8-element row segments first, then stores each segment
+// to its W row and, element by element, to the W^T column.  Otherwise,
+// element loads.
 __device__ void load_weights(WeightsSmem& W, const __nv_bfloat16* p, const float* pf) {
   const __nv_bfloat16 zero = __float2bfloat16(0.0f);
-  for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
-    const int r = i / 16, c = i % 16;
-    W.w1[r][c] = c < IN ? p[OW1 + r * IN + c] : zero;
-  }
-  for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
-    const int r = i / H, c = i % H;
-    W.w2[r][c] = p[OW2 + i];
-    W.w3[r][c] = p[OW3 + i];
-    W.w2t[c][r] = p[OW2 + i];
-    W.w3t[c][r] = p[OW3 + i];
-  }
-  for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
-    const int r = i / H, c = i % H;
-    W.w4[r][c] = r < OUT ? p[OW4 + r * H + c] : zero;
-  }
-  for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
-    const int r = i / 16, c = i % 16;
-    W.w4t[r][c] = c < OUT ? p[OW4 + c * H + r] : zero;
+  if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0) {
+    constexpr int N1 = H * IN / 8, N2 = H * H / 8, N4 = OUT * H / 8;
+    constexpr int NSEG = N1 + 2 * N2 + N4, PER = (NSEG + THREADS - 1) / THREADS;
+    static_assert(IN == 8 && (OW2 % 8) == 0 && (OW3 % 8) == 0 && (OW4 % 8) == 0,
+                  "16-byte row segments");
+    uint4 v[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * THREADS;
+      int off = 0;
+      if (i < N1) off = OW1 + 8 * i;
+      else if (i < N1 + N2) off = OW2 + 8 * (i - N1);
+      else if (i < N1 + 2 * N2) off = OW3 + 8 * (i - N1 - N2);
+      else if (i < NSEG) off = OW4 + 8 * (i - N1 - 2 * N2);
+      if (i < NSEG) v[k] = *reinterpret_cast<const uint4*>(p + off);
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + k * THREADS;
+      if (i >= NSEG) continue;
+      const uint32_t w[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+      if (i < N1) {
+        *reinterpret_cast<uint4*>(&W.w1[i][0]) = v[k];
+        *reinterpret_cast<uint4*>(&W.w1[i][8]) = make_uint4(0u, 0u, 0u, 0u);
+        continue;
+      }
+      const bool is4 = i >= N1 + 2 * N2;
+      const int j = i < N1 + N2 ? i - N1 : i < N1 + 2 * N2 ? i - N1 - N2 : i - N1 - 2 * N2;
+      const int r = j / (H / 8), c = 8 * (j % (H / 8));
+      __nv_bfloat16* row = is4 ? &W.w4[r][c] : i < N1 + N2 ? &W.w2[r][c] : &W.w3[r][c];
+      *reinterpret_cast<uint4*>(row) = v[k];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (is4) {
+          W.w4t[c + 2 * e][r] = bf_lo(w[e]);
+          W.w4t[c + 2 * e + 1][r] = bf_hi(w[e]);
+        } else if (i < N1 + N2) {
+          W.w2t[c + 2 * e][r] = bf_lo(w[e]);
+          W.w2t[c + 2 * e + 1][r] = bf_hi(w[e]);
+        } else {
+          W.w3t[c + 2 * e][r] = bf_lo(w[e]);
+          W.w3t[c + 2 * e + 1][r] = bf_hi(w[e]);
+        }
+      }
+    }
+    for (int i = threadIdx.x; i < (8 - OUT) * H; i += blockDim.x) W.w4[OUT + i / H][i % H] = zero;
+    for (int i = threadIdx.x; i < H * (16 - OUT); i += blockDim.x)
+      W.w4t[i / (16 - OUT)][OUT + i % (16 - OUT)] = zero;
+  } else {
+    for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
+      const int r = i / 16, c = i % 16;
+      W.w1[r][c] = c < IN ? p[OW1 + r * IN + c] : zero;
+    }
+    for (int i = threadIdx.x; i < H * H; i += blockDim.x) {
+      const int r = i / H, c = i % H;
+      W.w2[r][c] = p[OW2 + i];
+      W.w3[r][c] = p[OW3 + i];
+      W.w2t[c][r] = p[OW2 + i];
+      W.w3t[c][r] = p[OW3 + i];
+    }
+    for (int i = threadIdx.x; i < 8 * H; i += blockDim.x) {
+      const int r = i / H, c = i % H;
+      W.w4[r][c] = r < OUT ? p[OW4 + r * H + c] : zero;
+    }
+    for (int i = threadIdx.x; i < H * 16; i += blockDim.x) {
+      const int r = i / 16, c = i % 16;
+      W.w4t[r][c] = c < OUT ? p[OW4 + c * H + r] : zero;
+    }
   }
   for (int i = threadIdx.x; i < H; i += blockDim.x) {
     W.b1[i] = pf[OB1 + i];
@@ -181,8 +242,8 @@ __device__ __forceinline__ void features(const float* x, const int64_t* idx, int
 // With TRAIN, pre-activations go to the warp's z tiles and the transposed
 // inputs and activations to the block tiles T, at sample columns col ..
 // col + 15, for the backward pass.
-template <bool TRAIN>
-__device__ void forward16(const WeightsSmem& W, WarpZ* wz, BlockTiles* T, int col, const float* x,
+template <bool TRAIN, int CPW>
+__device__ void forward16(const WeightsSmem& W, WarpZ* wz, BlockTiles<CPW>* T, int col, const float* x,
                           const int64_t* idx, int64_t n, int64_t base, const CellGrid* grid,
                           const Std& sd, float* logit) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
@@ -221,33 +282,33 @@ __device__ void forward16(const WeightsSmem& W, WarpZ* wz, BlockTiles* T, int co
         mma(c[t], a[s], ld2(wr + 2 * q), ld2(wr + 8 + 2 * q));
       }
     }
-    if (TRAIN) {
-#pragma unroll
-      for (int t = 0; t < 8; ++t)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) wz->z[layer][4 * t + e][lane] = c[t][e];
-    }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const float v0 = silu(c[2 * s][0]), v1 = silu(c[2 * s][1]), v2 = silu(c[2 * s][2]),
-                  v3 = silu(c[2 * s][3]);
-      const float w0 = silu(c[2 * s + 1][0]), w1 = silu(c[2 * s + 1][1]),
-                  w2 = silu(c[2 * s + 1][2]), w3 = silu(c[2 * s + 1][3]);
-      a[s][0] = pack2(v0, v1);
-      a[s][1] = pack2(v2, v3);
-      a[s][2] = pack2(w0, w1);
-      a[s][3] = pack2(w2, w3);
+      // SiLU of tiles 2s (units 16s + 2q, +1) and 2s + 1 (units 16s + 8 + 2q,
+      // +1), rows g and g + 8; with TRAIN also SiLU'(z) = sg (1 + z (1 - sg))
+      float v[8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float z = c[2 * s + h][e], sg = sigm(z);
+          v[4 * h + e] = z * sg;
+          if (TRAIN) wz->ds[layer][4 * (2 * s + h) + e][lane] = sg * (1.0f + z * (1.0f - sg));
+        }
+      a[s][0] = pack2(v[0], v[1]);
+      a[s][1] = pack2(v[2], v[3]);
+      a[s][2] = pack2(v[4], v[5]);
+      a[s][3] = pack2(v[6], v[7]);
       if (TRAIN) {
-        const int c0 = 16 * s + 2 * q, c1 = 16 * s + 8 + 2 * q;
-        __nv_bfloat16 (*at)[LDT] = T->at[layer];
-        at[c0][col + g] = __float2bfloat16(v0);
-        at[c0 + 1][col + g] = __float2bfloat16(v1);
-        at[c0][col + g + 8] = __float2bfloat16(v2);
-        at[c0 + 1][col + g + 8] = __float2bfloat16(v3);
-        at[c1][col + g] = __float2bfloat16(w0);
-        at[c1 + 1][col + g] = __float2bfloat16(w1);
-        at[c1][col + g + 8] = __float2bfloat16(w2);
-        at[c1 + 1][col + g + 8] = __float2bfloat16(w3);
+        __nv_bfloat16 (*at)[BlockTiles<CPW>::LDT] = T->at[layer];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int u = 16 * s + 8 * h + 2 * q;
+          at[u][col + g] = __float2bfloat16(v[4 * h]);
+          at[u + 1][col + g] = __float2bfloat16(v[4 * h + 1]);
+          at[u][col + g + 8] = __float2bfloat16(v[4 * h + 2]);
+          at[u + 1][col + g + 8] = __float2bfloat16(v[4 * h + 3]);
+        }
       }
     }
   }
@@ -278,6 +339,7 @@ __device__ __forceinline__ void softmax_pair(float z0, float z1, float* p0, floa
 // units, samples contiguous: the col layout of B), FP32 accumulation in
 // registers; added once to the global gradient gW (row-major, n_in columns)
 // for rows < n_out and columns < n_in.
+template <int LDT>
 __device__ void block_dw(const __nv_bfloat16 (*dzt)[LDT], const __nv_bfloat16 (*at)[LDT], int m0,
                          int n0, int n_tiles, int n_out, int n_in, float* gW) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
@@ -285,7 +347,7 @@ __device__ void block_dw(const __nv_bfloat16 (*dzt)[LDT], const __nv_bfloat16 (*
 #pragma unroll
   for (int t = 0; t < 8; ++t) d[t][0] = d[t][1] = d[t][2] = d[t][3] = 0.0f;
 #pragma unroll 2
-  for (int ks = 0; ks < RS / 16; ++ks) {
+  for (int ks = 0; ks < (LDT - PK) / 16; ++ks) {
     uint32_t a[4];
     a[0] = ld2(&dzt[m0 + g][16 * ks + 2 * q]);
     a[1] = ld2(&dzt[m0 + g + 8][16 * ks + 2 * q]);
@@ -314,6 +376,7 @@ __device__ void block_dw(const __nv_bfloat16 (*dzt)[LDT], const __nv_bfloat16 (*
 
 // Write dZ (fragment layout: 16 samples x `tiles` 8-unit tiles) transposed
 // into the block tile dst at sample columns col .. col + 15.
+template <int LDT>
 __device__ __forceinline__ void store_dz(__nv_bfloat16 (*dst)[LDT], int col, const float (*dz)[4],
                                          int tiles) {
   const int lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
@@ -352,12 +415,14 @@ __device__ __forceinline__ void accumulate_db(const float (*dz)[4], int tiles, i
 // sums), then the four weight gradients of the round are formed as block
 // GEMMs (warp w: rows 16w .. 16w+15 of dW1..dW3, columns 16w .. 16w+15 of
 // dW4) and added to the global gradient.
+template <int CPW>
 __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, const float* pf,
                                                       Std sd, const float* x,
                                                       const uint8_t* label, const int64_t* idx,
                                                       int64_t n, float* grad, float* loss) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+  TrainSmem<CPW>& S = *reinterpret_cast<TrainSmem<CPW>*>(smem_raw);
+  constexpr int RS = BlockTiles<CPW>::RS, LDT = BlockTiles<CPW>::LDT;
   load_weights(S.w, pb, pf);
   for (int i = threadIdx.x; i < NGB; i += blockDim.x) S.gb[i] = 0.0f;
   // padding rows of the X^T and dZ4^T tiles (never written by the passes)
@@ -371,11 +436,11 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
   float loss_acc = 0.0f;
   const int64_t rounds = (n + RS - 1) / RS;
   for (int64_t rnd = blockIdx.x; rnd < rounds; rnd += gridDim.x) {
-    for (int c = 0; c < RS / (16 * WARPS); ++c) {
+    for (int c = 0; c < CPW; ++c) {
       const int col = 16 * (WARPS * c + warp);
       const int64_t base = rnd * RS + col;
       float lg[4];
-      forward16<true>(S.w, wz, &S.t, col, x, idx, n, base, nullptr, sd, lg);
+      forward16<true, CPW>(S.w, wz, &S.t, col, x, idx, n, base, nullptr, sd, lg);
       // softmax cross-entropy and dZ4 = (p - onehot) / n; rows past n and
       // rows without a target have dZ4 = 0 and so add nothing below
       float dz4[1][4] = {{0.f, 0.f, 0.f, 0.f}};
@@ -401,7 +466,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
         }
       }
       store_dz(S.t.dz4t, col, dz4, 1);
-      accumulate_db(dz4, 1, OUT, &S.gb[GB4]);
+      accumulate_db(dz4, 1, OUT, &S.gb[3 * H]);
       // dA3 = dZ4 W4: A operand from the dZ4 fragment (K padded 8 -> 16)
       uint32_t a[4][4];
       a[0][0] = pack2(dz4[0][0], dz4[0][1]);
@@ -422,7 +487,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_grad(const __nv_bfloat16* pb, c
           }
           // dZ = dA * SiLU'(Z)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) dz[t][e] *= dsilu(wz->z[layer][4 * t + e][lane]);
+          for (int e = 0; e < 4; ++e) dz[t][e] *= wz->ds[layer][4 * t + e][lane];
         }
         store_dz(S.t.dzt[layer], col, dz, 8);
         accumulate_db(dz, 8, H, &S.gb[GB1 + H * layer]);
@@ -468,7 +533,7 @@ __global__ void __launch_bounds__(THREADS) k_mlp_infer(const __nv_bfloat16* pb, 
        ch += (int64_t)gridDim.x * WARPS) {
     const int64_t base = ch * 16;
     float lg[4], p[4];
-    forward16<false>(W, nullptr, nullptr, 0, x, nullptr, n, base, use_grid ? &grid : nullptr, sd,
+    forward16<false, 1>(W, nullptr, nullptr, 0, x, nullptr, n, base, use_grid ? &grid : nullptr, sd,
                      lg);
     softmax_pair(lg[0], lg[1], &p[0], &p[1]);
     softmax_pair(lg[2], lg[3], &p[2], &p[3]);
@@ -713,26 +778,35 @@ CellGrid grid_of(const qcams_proposal_spec* s) {
   return g;
 }
 
+template <int CPW>
+cudaError_t launch_grad_cpw(const qcams_mlp* m, const float* x, const uint8_t* label,
+                            const int64_t* idx, int64_t n, float* loss_out, cudaStream_t st) {
+  const size_t smem = sizeof(TrainSmem<CPW>);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad<CPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int64_t grid = (n + BlockTiles<CPW>::RS - 1) / BlockTiles<CPW>::RS;
+  if (grid > sm_count()) grid = sm_count();
+  if (grid < 1) grid = 1;
+  k_mlp_grad<CPW><<<(unsigned)grid, THREADS, smem, st>>>(
+      reinterpret_cast<const __nv_bfloat16*>(m->params_bf16), m->params, std_of(m), x, label, idx,
+      n, m->grad, loss_out);
+  return cudaGetLastError();
+}
+
 int launch_grad(const qcams_mlp* m, const float* x, const uint8_t* label, const int64_t* idx,
                 int64_t n, float* loss_out, bool zero_loss, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(m->grad, 0, NP * sizeof(float), st);
   if (e == cudaSuccess && loss_out && zero_loss) e = cudaMemsetAsync(loss_out, 0, sizeof(float), st);
   if (e != cudaSuccess) return QCAMS_E_CUDA;
-  const size_t smem = sizeof(TrainSmem);
-  e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return QCAMS_E_CUDA;
-  // one block round of RS = 128 samples per block, at most one block per SM
-  // (the weights, the round's tiles and the warps' pre-activations take
-  // 203 KB of shared memory): a batch of 8,192 samples runs as 64 blocks of
-  // one round each, and each weight gradient element gets one vector atomic
-  // per block
-  int64_t grid = (n + RS - 1) / RS;
-  if (grid > sm_count()) grid = sm_count();
-  if (grid < 1) grid = 1;
-  k_mlp_grad<<<(unsigned)grid, THREADS, smem, st>>>(
-      reinterpret_cast<const __nv_bfloat16*>(m->params_bf16), m->params, std_of(m), x, label, idx,
-      n, m->grad, loss_out);
-  return status_of(cudaGetLastError());
+  // At most one block per SM (the weights, the round's tiles and the warps'
+  // SiLU' values take 155 KB of shared memory with 64-sample rounds, 203 KB
+  // with 128).  A batch that fits one 64-sample round per SM (8,192 samples:
+  // 128 blocks) takes that, the shortest block; larger batches take
+  // 128-sample rounds, half the rounds' global-atomic flushes.
+  e = (n + 63) / 64 <= sm_count() ? launch_grad_cpw<1>(m, x, label, idx, n, loss_out, st)
+                                  : launch_grad_cpw<2>(m, x, label, idx, n, loss_out, st);
+  return status_of(e);
 }
 
 int launch_adam(qcams_mlp* m, float lr, cudaStream_t st) {
