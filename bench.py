@@ -49,12 +49,12 @@ if ROOT not in sys.path:
 #   fraction of the FP64 pipe's instruction rate the kernel uses.
 FP64_FLOP_PER_STEP = 858
 FP64_INSTR_PER_STEP = 516
-#   FP32: 392 FFMA + 207 FMUL + 39 FADD = 1,031 FLOP and one DADD (the
-#   time) in 874 thread instructions per step (all pipes); the kernel is
+#   FP32: 393 FFMA + 178 FMUL + 39 FADD = 1,004 FLOP and one DADD (the
+#   time) in 787 thread instructions per step (all pipes); the kernel is
 #   bound by instruction issue, so issue_frac below is the fraction of the
 #   SMs' issue rate (4 warp instructions per SM per cycle) it uses.
-FP32_FLOP_PER_STEP = 1031
-FP32_THREAD_INSTR_PER_STEP = 874
+FP32_FLOP_PER_STEP = 1004
+FP32_THREAD_INSTR_PER_STEP = 787
 KERNEL_SOURCES = {
     64: ["integrate.cu", "elem64.cuh", "ff.cuh", "texp.cuh", "exp2_table.inc",
          "dp5_tableau.cuh"],
@@ -62,7 +62,7 @@ KERNEL_SOURCES = {
 }
 COUNTS_SOURCE_SHA256 = {
     64: "0d05ce86c76924d20f2f466b4986810db919333d08f23b8a62f307e96a7b9f5a",
-    32: "f3dd65025e870e50213e8a48fd029b38e5ba13044537446692c6624e00d85b21",
+    32: "183e3057913c4918104ed23054ecedc0ed56d845e712b5c20c96e7386b1c4acd",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of the same FP64 profile case (1,110,784 B read,

@@ -6,8 +6,8 @@
 // FP32 study of the sweep.  GB300 runs FP32 at 64x its FP64 rate, so this
 // path trades accuracy (tolerances ~1e-6) for throughput.
 //
-//  * Stages, forces and the error norm are FP32 (rsqrtf, __expf: the
-//    hardware 2^x of x log2 e, relative error below 2 + 1.2 |x| ulp; the
+//  * Stages, forces and the error norm are FP32 (the hardware 1/sqrt and
+//    2^x of x log2 e, relative error below 2 + 1.2 |x| ulp; the
 //    exponentials of the force law have |x| < 2 where the force matters and
 //    up to ~35 only for pairs far apart, whose forces are negligible).
 //  * Each step adds a small increment to a large state (|rho| ~ 30 bohr,
@@ -63,6 +63,25 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return r;
 }
 
+// 1/sqrt(s) (one MUFU instruction, about 1 ulp).  Flush-to-zero: s is a
+// squared pair distance, subnormal only for pairs closer than 1e-19 bohr,
+// where the lane fails on the infinite force it gets.
+__device__ __forceinline__ float rsqrt_approx(float s) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+  return r;
+}
+
+// x^(-1/10) for the step-size factor, as 2^(-log2(x) / 10) (two MUFU
+// instructions and a multiply).  x = 0 or subnormal gives +inf, which the
+// controller caps at the maximum growth factor as it does for a zero norm.
+__device__ __forceinline__ float pow_m01(float x) {
+  float l, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.1f * l));
+  return r;
+}
+
 // FP32 copies of the per-system constants (built on the host, so the kernel
 // never converts doubles in its inner loop).
 struct PairF {
@@ -95,7 +114,7 @@ __device__ __forceinline__ float ipowf_(float x, int n) {
 // 2 alpha De is folded into kf_morse)
 template <bool MORSE>
 __device__ __forceinline__ float pair_u(const PairF& q, float s) {
-  const float ri = rsqrtf(s);
+  const float ri = rsqrt_approx(s);
   const float r = s * ri;
   if (MORSE) {
     const float x = ex2_approx(fmaf(-q.l0, r, q.l1));   // e^{-alpha (r - re)}
@@ -214,14 +233,15 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
     float e = kTf.e[1] * L.acc[0][i];
 #pragma unroll
     for (int q = 3; q <= 7; ++q) e = fmaf(kTf.e[q], L.acc[q - 1][i], e);
-    ev[i] = h * e;
+    ev[i] = e;   // velocity error / h
     float ea = kTf.ea[1] * L.acc[0][i];
 #pragma unroll
     for (int q = 2; q <= 6; ++q)
       if (!dpEAZero(q)) ea = fmaf(kTf.ea[q], L.acc[q - 1][i], ea);
-    er[i] = hh * ea;
+    er[i] = ea;  // position error / h^2
   }
-  float sum = 0.0f;
+  // the factors h and h^2 multiply the two partial sums of squares once
+  float sum_r = 0.0f, sum_v = 0.0f;
   float vn[6], yv[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -231,15 +251,16 @@ __device__ __forceinline__ void attempt(const SysSetF& sys, const IntegParams& i
     const float qr = er[i] * rcp_approx(scr);
     const float scv = fmaf(ip.rtol_f, fmaxf(fabsf(L.vel[i]), fabsf(vn[i])), L.atv[i / 3]);
     const float qv = ev[i] * rcp_approx(scv);
-    sum = fmaf(qr, qr, fmaf(qv, qv, sum));
+    sum_r = fmaf(qr, qr, sum_r);
+    sum_v = fmaf(qv, qv, sum_v);
   }
-  const float en2 = sum * (1.0f / 12.0f);
+  const float en2 = fmaf(hh, sum_v, (hh * hh) * sum_r) * (1.0f / 12.0f);
   L.calls += 1;
   if (!(en2 == en2)) {   // NaN fails the lane; an overflowing norm just rejects
     L.status = QCAMS_LANE_FAIL_NAN;
     return;
   }
-  const float fac = 0.9f * __powf(en2, -0.1f);
+  const float fac = 0.9f * pow_m01(en2);
   const bool accept = en2 < 1.0f;
   float fa = (en2 == 0.0f) ? 10.0f : fminf(10.0f, fac);
   fa = L.rejected ? fminf(1.0f, fa) : fa;
