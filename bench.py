@@ -61,7 +61,7 @@ KERNEL_SOURCES = {
     32: ["integrate32.cu", "dp5_tableau.cuh"],
 }
 COUNTS_SOURCE_SHA256 = {
-    64: "0d05ce86c76924d20f2f466b4986810db919333d08f23b8a62f307e96a7b9f5a",
+    64: "f1fcf19f661d09c730edb1d975eb2d618bcee2fa8f46eb5153d2ee3445e480bd",
     32: "183e3057913c4918104ed23054ecedc0ed56d845e712b5c20c96e7386b1c4acd",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +

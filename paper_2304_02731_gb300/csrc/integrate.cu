@@ -71,6 +71,22 @@ __device__ __forceinline__ float err_mag(float x, unsigned& bad) {
   bad |= ((__float_as_uint(x) & 0x7f800000u) == 0x7f800000u) ? 1u : 0u;
   return fabsf(x);
 }
+// Approximate reciprocal (one MUFU instruction, about 1 ulp): the error
+// norm's scales are positive and far from the FP32 range limits (atol > 0).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+// x^(-1/10) for the step-size factor, as 2^(-log2(x) / 10) (two MUFU
+// instructions and a multiply).  x = 0 or subnormal gives +inf, which the
+// controller caps at the maximum growth factor as it does for a zero norm.
+__device__ __forceinline__ float pow_m01(float x) {
+  float l, r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.1f * l));
+  return r;
+}
 // Order of non-negative doubles equals the order of their bit patterns.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
@@ -424,11 +440,11 @@ __device__ __forceinline__ void lane_attempt(const SysSet& sys, const DevShape* 
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const float scr = fmaf(rt, fmaxf(mag_f(L.rho[i], ignore), mag_f(xn[i], ignore)), at);
-    const float qr = __fdividef(err_mag(er[i], bad) * hhf, scr);
+    const float qr = err_mag(er[i], bad) * hhf * rcp_approx(scr);
     sum = fmaf(qr, qr, sum);
     const float scv = fmaf(rt, fmaxf(mag_f(L.vel[i], ignore), mag_f(vn[i], ignore)),
                            i < 3 ? atv0 : atv1);
-    const float qv = __fdividef(err_mag(ev[i], bad) * hf, scv);
+    const float qv = err_mag(ev[i], bad) * hf * rcp_approx(scv);
     sum = fmaf(qv, qv, sum);
   }
   const float en2 = sum * (1.0f / 12.0f);
@@ -438,7 +454,7 @@ __device__ __forceinline__ void lane_attempt(const SysSet& sys, const DevShape* 
     return;
   }
   // en^(-1/5) = en2^(-1/10)
-  const float fac = 0.9f * __powf(en2, -0.1f);
+  const float fac = 0.9f * pow_m01(en2);
   const bool accept = en2 < 1.0f;
   float fa = (en2 == 0.0f) ? 10.0f : fminf(10.0f, fac);
   fa = L.rejected ? fminf(1.0f, fa) : fa;
