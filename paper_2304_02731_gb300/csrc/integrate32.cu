@@ -125,7 +125,14 @@ __device__ __forceinline__ float pair_u(const PairF& q, float s) {
     return q.c2 * fmaf(-x, x, x) * ri;
   }
   const float ri2 = ri * ri;
-  if (q.kind == QCAMS_LJ) return (q.c3 * ipowf_(ri, q.n) - q.c2 * ipowf_(ri, q.m)) * ri2;
+  if (q.kind == QCAMS_LJ) {
+    if (q.n == 6 && (q.m == 12 || q.m == 8)) {   // shared powers of 1/r^2
+      const float ri4 = ri2 * ri2, ri6 = ri4 * ri2;
+      const float h = q.m == 12 ? ri6 : ri4;
+      return fmaf(q.c3, ri6, -q.c2 * (h * h)) * ri2;
+    }
+    return (q.c3 * ipowf_(ri, q.n) - q.c2 * ipowf_(ri, q.m)) * ri2;
+  }
   const float ri6 = ri2 * ri2 * ri2;
   return (q.c3 * ri6 * ri - q.c2 * ex2_approx(-q.l1 * r)) * ri;   // e^{-B r}
 }
