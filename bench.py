@@ -62,7 +62,7 @@ KERNEL_SOURCES = {
 }
 COUNTS_SOURCE_SHA256 = {
     64: "f1fcf19f661d09c730edb1d975eb2d618bcee2fa8f46eb5153d2ee3445e480bd",
-    32: "183e3057913c4918104ed23054ecedc0ed56d845e712b5c20c96e7386b1c4acd",
+    32: "d3f34a9cb2505b08e412f46bd26cf80b51c2015d3df642ff21cbd4d700b9e1f2",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of the same FP64 profile case (1,110,784 B read,
