@@ -88,7 +88,8 @@ typedef struct {
                      guess"), used to bound root searches.  Buckingham
                      r_max_guess: a length near the short-range maximum
                      (the paper's "max").  Morse pairs need alpha re < 700
-                     (QCAMS_E_INVALID otherwise): e^{alpha (re - r)} stays
+                     and Buckingham pairs A B < e^700 (QCAMS_E_INVALID
+                     otherwise): e^{alpha (re - r)} and A B e^{-B r} stay
                      finite down to r = 0. */
 } qcams_pair;
 

@@ -113,7 +113,12 @@ int make_devpair(const qcams_pair& in, DevPair* out) {
       out->c3 = 6.0 * p[2];
       out->c4 = p[2];
       out->r_scale = p[3] > 0 ? p[3] : 1.0;
+      // the integrator forms A B e^{-B r} as e^{ln(A B) - B r}, with
+      // arguments below 700 for r > 0
+      out->lc2 = std::log(out->c2);
+      if (!(out->lc2 < 700.0)) return QCAMS_E_INVALID;
       out->ef0 = (float)out->c1;
+      out->ef1 = (float)out->lc2;
       return QCAMS_OK;
     default:
       return QCAMS_E_INVALID;

@@ -137,8 +137,11 @@ __device__ __forceinline__ double pair_u(const DevPair& q, double s, const doubl
     return q.c2 * fma(-x, x, x) * ri;
   }
   if (q.kind == QCAMS_BUCK) {
-    const double ri2 = ri * ri, ri6 = ri2 * ri2 * ri2;
-    return (q.c3 * ri6 * ri - q.c2 * texp_hint(-q.c1 * r, -q.ef0 * rf, T)) * ri;
+    // u = 6 C6 / r^8 - A B e^{-B r} / r, the exponential taking A B as the
+    // offset ln(A B) of its argument: 9 FP64 instructions
+    const double ri2 = ri * ri, ri4 = ri2 * ri2;
+    const double ex = texp_hint(fma(-q.c1, r, q.lc2), fmaf(-q.ef0, rf, q.ef1), T);
+    return fma(q.c3, ri4 * ri4, -(ex * ri));
   }
   return pot_g(q, ri, r);
 }

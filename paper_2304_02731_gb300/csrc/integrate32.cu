@@ -87,7 +87,8 @@ __device__ __forceinline__ float pow_m01(float x) {
 struct PairF {
   int kind, m, n, pad;
   float c0, c1, c2, c3, c4;
-  float l0, l1;   // exponent constants times log2 e: Morse c0, c1; Buckingham c1 (l1)
+  float l0, l1;   // exponent constants times log2 e: Morse c0, c1; Buckingham
+                  // ln(A B) (l0) and B (l1), so that 2^(l0 - l1 r) = A B e^{-B r}
 };
 struct SysF {
   float cA, cB, inv_mu12, inv_mu123, mu12, mu123;
@@ -133,8 +134,9 @@ __device__ __forceinline__ float pair_u(const PairF& q, float s) {
     }
     return (q.c3 * ipowf_(ri, q.n) - q.c2 * ipowf_(ri, q.m)) * ri2;
   }
-  const float ri6 = ri2 * ri2 * ri2;
-  return (q.c3 * ri6 * ri - q.c2 * ex2_approx(-q.l1 * r)) * ri;   // e^{-B r}
+  // Buckingham: 6 C6 / r^8 - A B e^{-B r} / r
+  const float ri4 = ri2 * ri2;
+  return fmaf(q.c3, ri4 * ri4, -(ex2_approx(fmaf(-q.l1, r, q.l0)) * ri));
 }
 
 template <bool MORSE>
@@ -502,7 +504,7 @@ SysSetF to_float(const SysSet& in) {
       g.c3 = (float)q.c3;
       g.c4 = (float)q.c4;
       const double log2e = 1.4426950408889634;
-      g.l0 = (float)(q.c0 * log2e);
+      g.l0 = (float)((q.kind == QCAMS_BUCK ? q.lc2 : q.c0) * log2e);
       g.l1 = (float)(q.c1 * log2e);
     }
   }

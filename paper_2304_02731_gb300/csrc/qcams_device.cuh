@@ -29,8 +29,11 @@ struct DevPair {
   double r_scale;  // a length near the well (root-search brackets)
   // FP32 copies of the exponent's coefficients, for the FP32 estimate of the
   // argument that the integrator's exponential rounds to its table index:
-  //   Morse: ef0 = alpha, ef1 = alpha re (x = ef1 - ef0 r);  Buck: ef0 = B (x = -B r)
+  //   Morse: ef0 = alpha, ef1 = alpha re (x = ef1 - ef0 r)
+  //   Buck:  ef0 = B, ef1 = ln(A B) (x = ln(A B) - B r: the exponential
+  //          returns A B e^{-B r} directly)
   float ef0, ef1;
+  double lc2;     // Buck: ln(A B), the exponent's offset for A B e^{-B r}
   // c0..c4 rounded to FP32, for the FP32 root location of the product analysis
   float cf[5];
   int32_t pad2;
