@@ -61,8 +61,8 @@ KERNEL_SOURCES = {
     32: ["integrate32.cu", "dp5_tableau.cuh"],
 }
 COUNTS_SOURCE_SHA256 = {
-    64: "f1fcf19f661d09c730edb1d975eb2d618bcee2fa8f46eb5153d2ee3445e480bd",
-    32: "d3f34a9cb2505b08e412f46bd26cf80b51c2015d3df642ff21cbd4d700b9e1f2",
+    64: "9fb8c7ece579adacf5d1e631e1a475c8ec9c820e934ec055f5eab44262e16bd9",
+    32: "70e2932855a88f714f4f7b48b180d82a8b03cd6726c5035bdfd2c9d94b9bb1c1",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of the same FP64 profile case (1,110,784 B read,
