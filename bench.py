@@ -57,7 +57,7 @@ FP32_FLOP_PER_STEP = 1004
 FP32_THREAD_INSTR_PER_STEP = 787
 KERNEL_SOURCES = {
     64: ["integrate.cu", "elem64.cuh", "ff.cuh", "texp.cuh", "exp2_table.inc",
-         "dp5_tableau.cuh"],
+         "dp5_tableau.cuh", "step_ctrl.cuh", "pair_force.cuh"],
     32: ["integrate32.cu", "dp5_tableau.cuh"],
 }
 COUNTS_SOURCE_SHA256 = {
@@ -117,7 +117,9 @@ def parse():
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="32: FP32 integrator with Kahan-compensated updates "
                          "(rtol 1e-6, atol 1e-8), FP64 everywhere else")
-    ap.add_argument("--persistent", type=int, default=1)
+    ap.add_argument("--persistent", type=int, default=1, choices=[0, 1, 2],
+                    help="0: one thread per trajectory; 1: persistent refill queue; "
+                         "2: three lanes per trajectory (FP64, small batches)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--tune", type=int, default=1,
@@ -310,11 +312,11 @@ def run_ours(args):
     wl = make_workload(args)
     # this rank's shard of the global id range (N x n lanes, weak scaling)
     wl.id_offset, _ = SH.shard_range(world * wl.n, rank, world)
-    integ = Q.make_integ(**wl.integ, persistent=bool(args.persistent), block=args.block,
+    integ = Q.make_integ(**wl.integ, persistent=args.persistent, block=args.block,
                          blocks_per_sm=args.blocks_per_sm, max_steps=args.max_steps,
                          precision=args.precision)
     tune = None
-    if args.tune and args.persistent and args.precision == 64:
+    if args.tune and args.persistent == 1 and args.precision == 64:
         # launch shape measured on a stratified sample of the workload
         from paper_2304_02731_gb300 import workloads as W
         per = max(1, min(256, wl.n // wl.n_cells))
@@ -489,9 +491,11 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": f"f{args.precision}",
         "data": "synthetic",
         "config": {"workload": wl.name, "trajectories_per_gpu": wl.n,
-                   "launch": ("persistent refill queue" if args.persistent else "one thread/lane")
+                   "launch": {0: "one thread/lane", 1: "persistent refill queue",
+                              2: "three lanes/trajectory"}[args.persistent]
                    + (", CUDA graph" if graph is not None else "")
-                   + f", block {integ.block or 128} x {integ.blocks_per_sm or 1}/SM variant",
+                   + (f", block {integ.block or 128} x {integ.blocks_per_sm or 1}/SM variant"
+                      if args.persistent != 2 else ", one warp (10 trajectories) per block"),
                    "autotune": tune,
                    "rtol": wl.integ["rtol"], "atol": wl.integ["atol"],
                    "arithmetic": ("FP64 state, forces and new-state sums; stage corrections, "
@@ -565,14 +569,16 @@ def time_steps(Q, wl, integ, steps, warmup, dev):
     return {"workload": wl.name, "trajectories": wl.n, "steps": steps, "warmup": warmup,
             "value": wl.n / (ms * 1e-3), "unit": "trajectories/s", "ms_per_step": ms,
             "integrate_ms": float(np.mean(integ_ms)), "analyze_ms": float(np.mean(analyze_ms)),
-            "launch": f"persistent refill queue, CUDA graph, block {integ.block or 128} x "
-                      f"{integ.blocks_per_sm or 1}/SM variant",
+            "launch": ("three lanes per trajectory, CUDA graph" if integ.persistent == 2 else
+                       f"persistent refill queue, CUDA graph, block {integ.block or 128} x "
+                       f"{integ.blocks_per_sm or 1}/SM variant"),
             "cls_counts_Q_RAC_RBC_D_AMBIG_FAIL": cls, "clocks": clock_info}
 
 
 def run_extras(args, dev):
     """Short measurements of the other workloads after the headline sweep
-    (single GPU, outside its timed region): the 1,000-lane plain study and
+    (single GPU, outside its timed region): the 1,000-lane plain study (three
+    lanes per trajectory, and one thread per trajectory for comparison) and
     the 2,000,000-lane mixed study in FP64 (autotuned launch shape), the
     sweep with the FP32 integrator, and the learned-proposal study."""
     import torch
@@ -589,8 +595,10 @@ def run_extras(args, dev):
         return best
 
     wl = W.plain_h2_ca()
-    out["plain_fp64"] = time_steps(Q, wl, tuned(wl, Q.make_integ(**wl.integ, persistent=True)),
+    out["plain_fp64"] = time_steps(Q, wl, Q.make_integ(**wl.integ, persistent=Q.LAUNCH_TRI),
                                    5, 3, dev)
+    out["plain_fp64_one_thread"] = time_steps(
+        Q, wl, tuned(wl, Q.make_integ(**wl.integ, persistent=True)), 5, 3, dev)
     wl = W.sweep_h2_ca()
     wl.integ = dict(W.INTEG_FP32)
     wl.name += "_fp32"

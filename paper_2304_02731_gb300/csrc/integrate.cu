@@ -45,71 +45,17 @@
 #include "dp5_tableau.cuh"
 #include "elem64.cuh"
 #include "ff.cuh"
+#include "step_ctrl.cuh"
+#include "pair_force.cuh"
 
 namespace qcams {
 namespace {
-
-// |x| as a float, truncated to 20 mantissa bits, using only integer
-// instructions on the high word of x; values below 2^-126 become 0 and
-// values above FLT_MAX saturate.  Sets `bad` for inf / NaN.
-__device__ __forceinline__ float mag_f(double x, unsigned& bad) {
-  const unsigned hi = (unsigned)__double2hiint(x) & 0x7fffffffu;
-  bad |= (hi >= 0x7ff00000u) ? 1u : 0u;
-  const int e = (int)(hi >> 20) - 896;
-  unsigned bits = ((unsigned)e << 23) | ((hi & 0x000fffffu) << 3);
-  bits = (e <= 0) ? 0u : bits;
-  bits = (e >= 255) ? 0x7f7fffffu : bits;
-  return __uint_as_float(bits);
-}
-__device__ __forceinline__ float signed_f(double x) {
-  unsigned bad = 0;
-  const float m = mag_f(x, bad);
-  return (__double2hiint(x) < 0) ? -m : m;
-}
-// |x| of an FP32 error estimate; sets `bad` for inf / NaN.
-__device__ __forceinline__ float err_mag(float x, unsigned& bad) {
-  bad |= ((__float_as_uint(x) & 0x7f800000u) == 0x7f800000u) ? 1u : 0u;
-  return fabsf(x);
-}
-// Approximate reciprocal (one MUFU instruction, about 1 ulp): the error
-// norm's scales are positive and far from the FP32 range limits (atol > 0).
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-// x^(-1/10) for the step-size factor, as 2^(-log2(x) / 10) (two MUFU
-// instructions and a multiply).  x = 0 or subnormal gives +inf, which the
-// controller caps at the maximum growth factor as it does for a zero norm.
-__device__ __forceinline__ float pow_m01(float x) {
-  float l, r;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-0.1f * l));
-  return r;
-}
-// Order of non-negative doubles equals the order of their bit patterns.
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
 // Coefficients in the constant bank: a DFMA takes a constant-bank operand at
 // full rate, so indexing this table with compile-time indices costs nothing.
 __constant__ RknTab kT = make_rkn_tab();
 
 // The coefficients of the float-float sums as float pairs.
-struct RknTabFF {
-  FFc a2[8][8];
-  FFc e[8];
-  FFc ea[8];
-};
-__host__ __device__ constexpr RknTabFF make_rkn_tab_ff() {
-  RknTabFF f{};
-  const RknTab t = make_rkn_tab();
-  for (int s = 1; s <= 7; ++s) {
-    f.e[s] = make_ffc(t.e[s]);
-    f.ea[s] = make_ffc(t.ea[s]);
-    for (int q = 1; q <= 7; ++q) f.a2[s][q] = make_ffc(t.a2[s][q]);
-  }
-  return f;
-}
 __constant__ RknTabFF kTff = make_rkn_tab_ff();
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -121,31 +67,6 @@ constexpr unsigned FULL = 0xffffffffu;
 //   dV/drho1 = g_AB r_AB - cB g_BC r_BC + cA g_CA r_CA,
 //   dV/drho2 = g_BC r_BC + g_CA r_CA,          g = V'(r)/r.
 // ---------------------------------------------------------------------------
-template <bool MORSE>
-__device__ __forceinline__ double pair_u(const DevPair& q, double s, const double* __restrict__ T) {
-  float rf;   // FP32 estimate of r, for the exponential's table index
-  const double ri = rsqrt_seeded(s, rf);
-  const double r = s * ri;
-  if (MORSE) {
-    // u = x (1 - x) / r, x = e^{-alpha (r - re)}; the factor 2 alpha De is in kf_morse
-    const double x = texp_hint(fma(-q.c0, r, q.c1), fmaf(-q.ef0, rf, q.ef1), T);
-    return fma(-x, x, x) * ri;
-  }
-  // generic kernels (mixed systems): u = V'(r)/r with the table exponential
-  if (q.kind == QCAMS_MORSE) {
-    const double x = texp_hint(fma(-q.c0, r, q.c1), fmaf(-q.ef0, rf, q.ef1), T);
-    return q.c2 * fma(-x, x, x) * ri;
-  }
-  if (q.kind == QCAMS_BUCK) {
-    // u = 6 C6 / r^8 - A B e^{-B r} / r, the exponential taking A B as the
-    // offset ln(A B) of its argument: 9 FP64 instructions
-    const double ri2 = ri * ri, ri4 = ri2 * ri2;
-    const double ex = texp_hint(fma(-q.c1, r, q.lc2), fmaf(-q.ef0, rf, q.ef1), T);
-    return fma(q.c3, ri4 * ri4, -(ex * ri));
-  }
-  return pot_g(q, ri, r);
-}
-
 template <bool MORSE>
 __device__ __forceinline__ void accel(const DevSys& S, const double* __restrict__ T,
                                       const double* x, double* a, double* s2) {
@@ -775,6 +696,7 @@ cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const In
     else k_integrate_fixed<false><<<grid, 128, 0, st>>>(sys, ip, b, ctx.counters);
     return cudaGetLastError();
   }
+  if (persistent == 2) return launch_integrate_tri(sys, shapes, ip, b, ctx.counters, st, morse);
   const int v = find_variant(block, blocks_per_sm);
   if (v < 0) return cudaErrorInvalidValue;
   return morse ? launch_variant<true>(v, sys, shapes, ip, b, persistent, ctx, st, nullptr)

@@ -61,6 +61,12 @@ cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const In
                              const DevBatch& b, int precision, int persistent, int block,
                              int blocks_per_sm, Ctx& ctx, cudaStream_t st);
 
+// FP64 integrator for small batches, three lanes per trajectory
+// (integrate_tri.cu).
+cudaError_t launch_integrate_tri(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
+                                 const DevBatch& b, unsigned long long* counters,
+                                 cudaStream_t st, bool all_morse);
+
 // FP32 integrator with compensated state updates (integrate32.cu).
 cudaError_t launch_integrate32(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
                                const DevBatch& b, int persistent, Ctx& ctx, cudaStream_t st,

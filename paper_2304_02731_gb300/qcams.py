@@ -206,11 +206,15 @@ def systems_array(systems):
     return arr
 
 
+# qcams_integ.persistent = 2: three lanes per trajectory (FP64, small batches)
+LAUNCH_TRI = 2
+
+
 def make_integ(rtol=1e-10, atol=1e-12, r_stop=35.0, t_stop=15.0, h_fixed=0.0,
                gb_sigma=GB_SIGMA_DEFAULT, max_steps=1_000_000, fixed_step=False, precision=64,
                persistent=False, block=0, blocks_per_sm=0) -> Integ:
     return Integ(rtol, atol, r_stop, t_stop, h_fixed, gb_sigma, int(max_steps),
-                 int(bool(fixed_step)), int(precision), int(bool(persistent)), int(block),
+                 int(bool(fixed_step)), int(precision), int(persistent), int(block),
                  int(blocks_per_sm), 0)
 
 
