@@ -61,7 +61,7 @@ KERNEL_SOURCES = {
     32: ["integrate32.cu", "dp5_tableau.cuh"],
 }
 COUNTS_SOURCE_SHA256 = {
-    64: "9fb8c7ece579adacf5d1e631e1a475c8ec9c820e934ec055f5eab44262e16bd9",
+    64: "814f85a15d09e4cd217bd32d64ff63baa6daab15e9f1e86d354b35534e394cb0",
     32: "70e2932855a88f714f4f7b48b180d82a8b03cd6726c5035bdfd2c9d94b9bb1c1",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
