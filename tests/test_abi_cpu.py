@@ -106,6 +106,8 @@ def test_entry_points_reject_bad_arguments_without_a_device(Q):
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
     bad = Q.make_integ(persistent=Q.LAUNCH_TRI, precision=32)
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
+    bad = Q.make_integ(persistent=Q.LAUNCH_TRI, fixed_step=True, h_fixed=0.1)
+    assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
     assert L.qcams_init_states(sysarr, 1, None, None, None, None, 30.0, 0, 0, None,
                                C.byref(b), None) == -1
     b.n = -1
