@@ -61,7 +61,7 @@ KERNEL_SOURCES = {
     32: ["integrate32.cu", "dp5_tableau.cuh"],
 }
 COUNTS_SOURCE_SHA256 = {
-    64: "814f85a15d09e4cd217bd32d64ff63baa6daab15e9f1e86d354b35534e394cb0",
+    64: "fd6d5ddd0d217fb2e65a0cdb9d954a16fe94748819544d38a5e6081d586d4c95",
     32: "70e2932855a88f714f4f7b48b180d82a8b03cd6726c5035bdfd2c9d94b9bb1c1",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
@@ -117,9 +117,9 @@ def parse():
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="32: FP32 integrator with Kahan-compensated updates "
                          "(rtol 1e-6, atol 1e-8), FP64 everywhere else")
-    ap.add_argument("--persistent", type=int, default=1, choices=[0, 1, 2],
+    ap.add_argument("--persistent", type=int, default=1, choices=[0, 1, 2, 3],
                     help="0: one thread per trajectory; 1: persistent refill queue; "
-                         "2: three lanes per trajectory (FP64, small batches)")
+                         "2 / 3: three / six lanes per trajectory (FP64, small batches)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--tune", type=int, default=1,
@@ -492,10 +492,12 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": wl.name, "trajectories_per_gpu": wl.n,
                    "launch": {0: "one thread/lane", 1: "persistent refill queue",
-                              2: "three lanes/trajectory"}[args.persistent]
+                              2: "three lanes/trajectory",
+                              3: "six lanes/trajectory"}[args.persistent]
                    + (", CUDA graph" if graph is not None else "")
                    + (f", block {integ.block or 128} x {integ.blocks_per_sm or 1}/SM variant"
-                      if args.persistent != 2 else ", one warp (10 trajectories) per block"),
+                      if args.persistent < 2 else
+                      f", one warp ({10 if args.persistent == 2 else 5} trajectories) per block"),
                    "autotune": tune,
                    "rtol": wl.integ["rtol"], "atol": wl.integ["atol"],
                    "arithmetic": ("FP64 state, forces and new-state sums; stage corrections, "
@@ -569,7 +571,8 @@ def time_steps(Q, wl, integ, steps, warmup, dev):
     return {"workload": wl.name, "trajectories": wl.n, "steps": steps, "warmup": warmup,
             "value": wl.n / (ms * 1e-3), "unit": "trajectories/s", "ms_per_step": ms,
             "integrate_ms": float(np.mean(integ_ms)), "analyze_ms": float(np.mean(analyze_ms)),
-            "launch": ("three lanes per trajectory, CUDA graph" if integ.persistent == 2 else
+            "launch": (f"{'three' if integ.persistent == 2 else 'six'} lanes per trajectory, "
+                       "CUDA graph" if integ.persistent >= 2 else
                        f"persistent refill queue, CUDA graph, block {integ.block or 128} x "
                        f"{integ.blocks_per_sm or 1}/SM variant"),
             "cls_counts_Q_RAC_RBC_D_AMBIG_FAIL": cls, "clocks": clock_info}
@@ -577,7 +580,7 @@ def time_steps(Q, wl, integ, steps, warmup, dev):
 
 def run_extras(args, dev):
     """Short measurements of the other workloads after the headline sweep
-    (single GPU, outside its timed region): the 1,000-lane plain study (three
+    (single GPU, outside its timed region): the 1,000-lane plain study (six
     lanes per trajectory, and one thread per trajectory for comparison) and
     the 2,000,000-lane mixed study in FP64 (autotuned launch shape), the
     sweep with the FP32 integrator, and the learned-proposal study."""
@@ -595,7 +598,7 @@ def run_extras(args, dev):
         return best
 
     wl = W.plain_h2_ca()
-    out["plain_fp64"] = time_steps(Q, wl, Q.make_integ(**wl.integ, persistent=Q.LAUNCH_TRI),
+    out["plain_fp64"] = time_steps(Q, wl, Q.make_integ(**wl.integ, persistent=Q.LAUNCH_HEX),
                                    5, 3, dev)
     out["plain_fp64_one_thread"] = time_steps(
         Q, wl, tuned(wl, Q.make_integ(**wl.integ, persistent=True)), 5, 3, dev)

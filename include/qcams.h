@@ -143,13 +143,14 @@ typedef struct {
   int32_t persistent;  /* 1 = persistent refill-queue launch (finished lanes
                           take the next trajectory from a device counter);
                           0 = one thread per trajectory;
-                          2 = three lanes per trajectory (FP64 adaptive
-                          steps only, else QCAMS_E_INVALID; block and
-                          blocks_per_sm are not used): each step takes
-                          about 2.5x fewer warp-wide FP64 instructions,
-                          for batches too small to fill the GPU (below
-                          ~10,000 trajectories); a warp holds 10
-                          trajectories instead of 32 */
+                          2 = three lanes per trajectory, 3 = six lanes
+                          per trajectory (FP64 adaptive steps only, else
+                          QCAMS_E_INVALID; block and blocks_per_sm are not
+                          used): a step takes about 2.6x (3x) fewer
+                          warp-wide FP64 instructions, for batches too
+                          small to fill the GPU (below ~10,000
+                          trajectories); a warp holds 10 (5) trajectories
+                          instead of 32 */
   int32_t block;       /* threads per block (0 = 128) */
   int32_t blocks_per_sm; /* resident blocks per SM the integrator variant is
                             compiled for (its __launch_bounds__ minimum, which

@@ -183,8 +183,8 @@ int make_integ_params(const qcams_integ* in, IntegParams* ip) {
   }
   if (in->precision != 64 && in->precision != 32 && in->precision != 0) return QCAMS_E_INVALID;
   if (in->precision == 32 && in->fixed_step) return QCAMS_E_INVALID;
-  if (in->persistent < 0 || in->persistent > 2) return QCAMS_E_INVALID;
-  if (in->persistent == 2 && (in->precision == 32 || in->fixed_step)) return QCAMS_E_INVALID;
+  if (in->persistent < 0 || in->persistent > 3) return QCAMS_E_INVALID;
+  if (in->persistent >= 2 && (in->precision == 32 || in->fixed_step)) return QCAMS_E_INVALID;
   if (in->block < 0 || in->block > 1024 || in->blocks_per_sm < 0) return QCAMS_E_INVALID;
   if (!in->fixed_step && !integrate_shape_supported(in->block, in->blocks_per_sm))
     return QCAMS_E_INVALID;

@@ -696,7 +696,9 @@ cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const In
     else k_integrate_fixed<false><<<grid, 128, 0, st>>>(sys, ip, b, ctx.counters);
     return cudaGetLastError();
   }
-  if (persistent == 2) return launch_integrate_tri(sys, shapes, ip, b, ctx.counters, st, morse);
+  if (persistent == 2 || persistent == 3)
+    return launch_integrate_grouped(sys, shapes, ip, b, persistent == 2 ? 3 : 6, ctx.counters, st,
+                                    morse);
   const int v = find_variant(block, blocks_per_sm);
   if (v < 0) return cudaErrorInvalidValue;
   return morse ? launch_variant<true>(v, sys, shapes, ip, b, persistent, ctx, st, nullptr)

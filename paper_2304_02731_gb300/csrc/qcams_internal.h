@@ -61,11 +61,12 @@ cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const In
                              const DevBatch& b, int precision, int persistent, int block,
                              int blocks_per_sm, Ctx& ctx, cudaStream_t st);
 
-// FP64 integrator for small batches, three lanes per trajectory
+// FP64 integrator for small batches, `lanes` = 3 or 6 lanes per trajectory
 // (integrate_tri.cu).
-cudaError_t launch_integrate_tri(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
-                                 const DevBatch& b, unsigned long long* counters,
-                                 cudaStream_t st, bool all_morse);
+cudaError_t launch_integrate_grouped(const SysSet& sys, const DevShape* shapes,
+                                     const IntegParams& ip, const DevBatch& b, int lanes,
+                                     unsigned long long* counters, cudaStream_t st,
+                                     bool all_morse);
 
 // FP32 integrator with compensated state updates (integrate32.cu).
 cudaError_t launch_integrate32(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,

@@ -206,8 +206,10 @@ def systems_array(systems):
     return arr
 
 
-# qcams_integ.persistent = 2: three lanes per trajectory (FP64, small batches)
+# qcams_integ.persistent = 2 / 3: three / six lanes per trajectory (FP64,
+# small batches)
 LAUNCH_TRI = 2
+LAUNCH_HEX = 3
 
 
 def make_integ(rtol=1e-10, atol=1e-12, r_stop=35.0, t_stop=15.0, h_fixed=0.0,

@@ -101,12 +101,14 @@ def test_entry_points_reject_bad_arguments_without_a_device(Q):
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
     bad = Q.make_integ(precision=16)
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
-    # launch modes 0, 1, 2 only; three lanes per trajectory is FP64 only
-    bad = Q.make_integ(persistent=3)
+    # launch modes 0-3 only; three or six lanes per trajectory are FP64 only
+    bad = Q.make_integ(persistent=4)
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
     bad = Q.make_integ(persistent=Q.LAUNCH_TRI, precision=32)
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
     bad = Q.make_integ(persistent=Q.LAUNCH_TRI, fixed_step=True, h_fixed=0.1)
+    assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
+    bad = Q.make_integ(persistent=Q.LAUNCH_HEX, precision=32)
     assert L.qcams_run_batch(sysarr, 1, C.byref(bad), C.byref(b), None) == -1
     assert L.qcams_init_states(sysarr, 1, None, None, None, None, 30.0, 0, 0, None,
                                C.byref(b), None) == -1

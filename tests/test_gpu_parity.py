@@ -139,10 +139,10 @@ def _adaptive_pair(Q, oracle, wl, integ_kw=None, persistent=False):
     return batch, g, hist, cells, groups, st, res
 
 
-@pytest.mark.parametrize("launch", [0, 2], ids=["thread", "triplet"])
+@pytest.mark.parametrize("launch", [0, 2, 3], ids=["thread", "three_lanes", "six_lanes"])
 def test_adaptive_plain_study_parity(Q, oracle, launch):
     """200 lanes of the plain H2 + Ca study (E = 0.1, b = 0..6), one thread
-    per lane and three lanes per lane (triplet).  Every lane
+    per lane and three or six lanes per lane.  Every lane
     that separated on both sides is a quench on both.  Lanes that form a
     long-lived Ca-H2 complex can still be inside it at t_max: whether such a
     complex breaks up before t_max depends on rounding-level details, so the
@@ -189,11 +189,11 @@ def test_adaptive_plain_study_parity(Q, oracle, launch):
     assert np.all(g["cls"][sep] == 0)
 
 
-@pytest.mark.parametrize("launch", [0, 2], ids=["thread", "triplet"])
+@pytest.mark.parametrize("launch", [0, 2, 3], ids=["thread", "three_lanes", "six_lanes"])
 def test_tiny_batch_field_by_field(Q, oracle, launch):
     """32 lanes run by the oracle one by one, every per-lane output compared
-    (one thread per lane, and three lanes per lane whose sums over the
-    triplet take another rounding order):
+    (one thread per lane, and three or six lanes per lane whose sums over
+    the group take another rounding order):
     18 lanes of the plain study (b = 0, 3, 6 bohr: direct collisions) and 14
     of the sweep (its lowest and highest energies).  Integers (status,
     class, accepted and rejected steps, v_t, j_t) agree exactly on every
@@ -336,12 +336,13 @@ def test_empty_and_invalid_lanes(Q):
     Q.run_batch([W.SYS_H2_CA_MORSE], batch, Q.make_integ())
     torch.cuda.synchronize()
     st = batch.status.cpu().numpy()
-    tri = Q.Batch.empty(n, "cuda", sys_id=[0, 0, 0, 3, 0, 0, 0, -1])
-    Q.init_states([W.SYS_H2_CA_MORSE], tri, E, b, v, j, 30.0, 0)
-    Q.run_batch([W.SYS_H2_CA_MORSE], tri, Q.make_integ(persistent=Q.LAUNCH_TRI))
-    torch.cuda.synchronize()
-    assert np.array_equal(tri.status.cpu().numpy(), st)
-    assert np.all(np.isfinite(tri.y.cpu().numpy()))
+    for launch in (Q.LAUNCH_TRI, Q.LAUNCH_HEX):
+        grp = Q.Batch.empty(n, "cuda", sys_id=[0, 0, 0, 3, 0, 0, 0, -1])
+        Q.init_states([W.SYS_H2_CA_MORSE], grp, E, b, v, j, 30.0, 0)
+        Q.run_batch([W.SYS_H2_CA_MORSE], grp, Q.make_integ(persistent=launch))
+        torch.cuda.synchronize()
+        assert np.array_equal(grp.status.cpu().numpy(), st), launch
+        assert np.all(np.isfinite(grp.y.cpu().numpy()))
     # valid; E <= 0; R <= b; system out of range; v beyond the table; NaN E;
     # NaN b; negative system index
     assert list(st) == [2, 9, 9, 9, 8, 9, 9, 9]
@@ -417,11 +418,11 @@ def test_per_lane_failure_statuses(Q):
     and every other lane's outcome is unchanged: a NaN in the state gives
     FAIL_NAN, a step size below 2^-49 of the time (t = 1e15, h = 1e-3)
     FAIL_HMIN, and a cap of 20 attempts FAIL_MAXSTEPS with class FAIL.
-    FP64 one-thread-per-lane, persistent and three-lane launches, and the
-    FP32 integrator."""
+    FP64 one-thread-per-lane, persistent, three- and six-lane launches, and
+    the FP32 integrator."""
     import torch
     wl = W.plain_h2_ca(per_b=8)
-    for prec, persistent in [(64, False), (64, True), (64, 2), (32, True)]:
+    for prec, persistent in [(64, False), (64, True), (64, 2), (64, 3), (32, True)]:
         kw = W.INTEG_FP64 if prec == 64 else W.INTEG_FP32
         integ = Q.make_integ(**kw, persistent=persistent, precision=prec)
         ref, _, _, _ = Q.run_workload(wl, integ, finalize=False)
@@ -452,7 +453,7 @@ def test_per_lane_failure_statuses(Q):
         assert np.all(h["nsteps"] + h["nrej"] == 20)
 
 
-@pytest.mark.parametrize("launch", [0, 2], ids=["thread", "triplet"])
+@pytest.mark.parametrize("launch", [0, 2, 3], ids=["thread", "three_lanes", "six_lanes"])
 def test_mixed_potentials_parity(Q, oracle, launch):
     """Buckingham / LJ(12,6) / LJ(8,6) Ca-H with mixed (v, j, E, b): 3,000
     lanes of the mixed study (about 1,000 per system) run by the GPU and,
@@ -776,7 +777,7 @@ def test_stop_and_collapse_rules_on_constructed_states(Q, oracle):
             o = oracle.run_adaptive([osys[k] for k in sys_ids], sid,
                                     oracle.make_integ(**kw), y0.copy(), ts, E0,
                                     np.zeros(len(ls), np.int32))
-            for persistent in ((False, True, 2) if prec == 64 else (True,)):
+            for persistent in ((False, True, 2, 3) if prec == 64 else (True,)):
                 b = Q.Batch.empty(len(ls), "cuda", sys_id=sid)
                 b.set_state(y0)
                 b.f64["t_scale"].copy_(torch.as_tensor(ts))

@@ -51,9 +51,10 @@ def _run(Q, wl, entry, persistent, **integ_kw):
 def test_noalloc_matches_run_batch_on_two_calls(Q):
     # call 1: all-Morse plain study lanes (persistent launch);
     # call 2: mixed Buckingham / LJ systems (one thread per lane);
-    # calls 3, 4: both with three lanes per trajectory
+    # calls 3, 4: three lanes per trajectory; call 5: six lanes
     cases = [(W.plain_h2_ca(per_b=12), True), (W.mixed_ca_h(n=120, seed=5), False),
-             (W.plain_h2_ca(per_b=12), Q.LAUNCH_TRI), (W.mixed_ca_h(n=121, seed=5), Q.LAUNCH_TRI)]
+             (W.plain_h2_ca(per_b=12), Q.LAUNCH_TRI), (W.mixed_ca_h(n=121, seed=5), Q.LAUNCH_TRI),
+             (W.mixed_ca_h(n=61, seed=5), Q.LAUNCH_HEX)]
     for wl, persistent in cases:
         ref = _run(Q, wl, "qcams_run_batch", persistent)
         got = _run(Q, wl, "qcams_run_batch_noalloc", persistent)
