@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqcams.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["api.cu", "integrate.cu", "integrate_tri.cu", "integrate32.cu", "peak.cu", "noalloc.cu",
+SOURCES = ["api.cu", "integrate.cu", "integrate_grp.cu", "integrate32.cu", "peak.cu", "noalloc.cu",
            "mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

@@ -1,7 +1,7 @@
 // The pair-force factor u = V'(r)/r of one pair at squared distance s, as
 // the FP64 integrators form it (Sec. 3.2 potentials): the reciprocal square
 // root and the exponential of elem64.cuh, 10 FP64 instructions for a Morse
-// pair.  Shared by the one-thread-per-trajectory and the three-lane
+// pair.  Shared by the one-thread-per-trajectory and the lane-group
 // integrators.
 #pragma once
 

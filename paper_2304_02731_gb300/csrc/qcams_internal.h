@@ -62,7 +62,7 @@ cudaError_t launch_integrate(const SysSet& sys, const DevShape* shapes, const In
                              int blocks_per_sm, Ctx& ctx, cudaStream_t st);
 
 // FP64 integrator for small batches, `lanes` = 3 or 6 lanes per trajectory
-// (integrate_tri.cu).
+// (integrate_grp.cu).
 cudaError_t launch_integrate_grouped(const SysSet& sys, const DevShape* shapes,
                                      const IntegParams& ip, const DevBatch& b, int lanes,
                                      unsigned long long* counters, cudaStream_t st,

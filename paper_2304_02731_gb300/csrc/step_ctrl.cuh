@@ -1,5 +1,5 @@
 // Pieces shared by the FP64 integrators (one thread per trajectory in
-// integrate.cu, three lanes per trajectory in integrate_tri.cu): the FP32
+// integrate.cu, a group of lanes per trajectory in integrate_grp.cu): the FP32
 // magnitudes the step-size controller works with, the controller's MUFU
 // arithmetic, and the float-float copy of the Runge-Kutta-Nystrom
 // coefficients (Dormand-Prince 5(4), Sec. 3.2).
