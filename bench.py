@@ -326,7 +326,8 @@ def run_ours(args):
         best, table = Q.autotune(sw.systems, sb, integ, max_attempts=1500)
         integ = best
         tune = {"sample_lanes": sw.n, "max_attempts": 1500,
-                "chosen": {"block": best.block, "blocks_per_sm": best.blocks_per_sm},
+                "chosen": {"persistent": best.persistent, "block": best.block,
+                           "blocks_per_sm": best.blocks_per_sm},
                 "variants": [{k: (round(v, 4) if isinstance(v, float) else v)
                               for k, v in r.items()} for r in table]}
         del sb
@@ -493,11 +494,11 @@ def run_ours(args):
         "config": {"workload": wl.name, "trajectories_per_gpu": wl.n,
                    "launch": {0: "one thread/lane", 1: "persistent refill queue",
                               2: "three lanes/trajectory",
-                              3: "six lanes/trajectory"}[args.persistent]
+                              3: "six lanes/trajectory"}[integ.persistent]
                    + (", CUDA graph" if graph is not None else "")
                    + (f", block {integ.block or 128} x {integ.blocks_per_sm or 1}/SM variant"
-                      if args.persistent < 2 else
-                      f", one warp ({10 if args.persistent == 2 else 5} trajectories) per block"),
+                      if integ.persistent < 2 else
+                      f", one warp ({10 if integ.persistent == 2 else 5} trajectories) per block"),
                    "autotune": tune,
                    "rtol": wl.integ["rtol"], "atol": wl.integ["atol"],
                    "arithmetic": ("FP64 state, forces and new-state sums; stage corrections, "
@@ -580,8 +581,8 @@ def time_steps(Q, wl, integ, steps, warmup, dev):
 
 def run_extras(args, dev):
     """Short measurements of the other workloads after the headline sweep
-    (single GPU, outside its timed region): the 1,000-lane plain study (six
-    lanes per trajectory, and one thread per trajectory for comparison) and
+    (single GPU, outside its timed region): the 1,000-lane plain study (the
+    autotuner's launch, and one thread per trajectory for comparison) and
     the 2,000,000-lane mixed study in FP64 (autotuned launch shape), the
     sweep with the FP32 integrator, and the learned-proposal study."""
     import torch
@@ -598,10 +599,10 @@ def run_extras(args, dev):
         return best
 
     wl = W.plain_h2_ca()
-    out["plain_fp64"] = time_steps(Q, wl, Q.make_integ(**wl.integ, persistent=Q.LAUNCH_HEX),
+    out["plain_fp64"] = time_steps(Q, wl, tuned(wl, Q.make_integ(**wl.integ, persistent=True)),
                                    5, 3, dev)
     out["plain_fp64_one_thread"] = time_steps(
-        Q, wl, tuned(wl, Q.make_integ(**wl.integ, persistent=True)), 5, 3, dev)
+        Q, wl, Q.make_integ(**wl.integ, persistent=True, block=64, blocks_per_sm=1), 5, 3, dev)
     wl = W.sweep_h2_ca()
     wl.integ = dict(W.INTEG_FP32)
     wl.name += "_fp32"

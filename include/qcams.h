@@ -383,24 +383,31 @@ int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys, const qcams_
                             qcams_batch* batch, void* cuda_stream);
 
 /*
- * Launch-shape autotuner for the persistent integrator (the paper has no
- * counterpart; it sizes the GPU launch).  `sample` is an initialised batch
- * (device SoA, status READY) representative of the workload; for every
- * supported (block, blocks_per_sm) variant the integrator runs on it, from
- * the same saved initial state, with at most `max_attempts` step attempts
- * per lane, and the attempted lane-steps per second are measured with CUDA
- * events.  The sample's state is restored afterwards.  results (host, room
- * for QCAMS_TUNE_MAX_VARIANTS entries) receives one entry per variant,
- * *n_results their number, and *best a copy of *integ with the fastest
- * shape and persistent = 1; shapes within 2 % of the fastest count as a tie,
- * which goes to the smallest block (then the fewest blocks per SM).  Synchronous; allocates a temporary copy of the
- * sample state (~121 bytes per lane) with cudaMallocAsync.
+ * Launch autotuner for the FP64 integrator (the paper has no counterpart;
+ * it sizes the GPU launch).  `sample` is an initialised batch (device SoA,
+ * status READY) representative of the workload, ideally the workload
+ * itself when it is small; the integrator runs on it, from the same saved
+ * initial state, with at most `max_attempts` step attempts per lane, once
+ * for every supported (block, blocks_per_sm) variant of the persistent
+ * launch and once for each lane-group launch (persistent = 2 and 3, one
+ * warp per block), and the attempted lane-steps per second are measured
+ * with CUDA events.  The sample's state is restored afterwards.  results
+ * (host, room for QCAMS_TUNE_MAX_VARIANTS entries) receives one entry per
+ * launch, *n_results their number, and *best a copy of *integ with the
+ * fastest launch (its persistent, block and blocks_per_sm).  Persistent
+ * shapes within 2 % of the fastest persistent shape count as a tie, which
+ * goes to the smallest block (then the fewest blocks per SM); a lane-group
+ * launch is chosen only if it is strictly the fastest.  Synchronous;
+ * allocates a temporary copy of the sample state (~121 bytes per lane) with
+ * cudaMallocAsync.
  */
 #define QCAMS_TUNE_MAX_VARIANTS 16
 typedef struct {
   int32_t block, blocks_per_sm;  /* the variant */
   int32_t regs;                  /* registers per thread */
   int32_t resident_blocks;       /* occupancy: blocks per SM */
+  int32_t persistent;            /* launch mode: 1 persistent, 2 / 3 lane groups */
+  int32_t pad;
   double ms;                     /* integrator time on the sample */
   double lane_steps_per_s;       /* attempted lane-steps per second */
 } qcams_tune_result;

@@ -1008,16 +1008,21 @@ int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* in
   IntegParams tip = ip;
   if (tip.max_steps > max_attempts) tip.max_steps = max_attempts;
   const bool morse = integrate_all_morse(ss);
-  const int nv = integrate_variant_count();
+  // the persistent shapes, then the two lane-group launches
+  const int nv_shapes = integrate_variant_count();
+  const int nv = nv_shapes + 2;
   int best_v = -1;
   double best_rate = -1.0;
   for (int v = 0; v < nv && v < QCAMS_TUNE_MAX_VARIANTS && e == cudaSuccess; ++v) {
-    int block = 0, bps = 0;
-    integrate_variant_shape(v, &block, &bps);
+    int block = 32, bps = 0, mode = 1;
+    if (v < nv_shapes)
+      integrate_variant_shape(v, &block, &bps);
+    else
+      mode = v == nv_shapes ? 2 : 3;
     e = copy_all(false);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[0], st);
     if (e == cudaSuccess)
-      e = launch_integrate(ss, ctx->shapes, tip, d, 64, 1, block, bps, *ctx, st);
+      e = launch_integrate(ss, ctx->shapes, tip, d, 64, mode, block, bps, *ctx, st);
     if (e == cudaSuccess) e = cudaEventRecord(ctx->ev[1], st);
     unsigned long long cnt[2] = {0, 0};
     if (e == cudaSuccess)
@@ -1029,10 +1034,16 @@ int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* in
     qcams_tune_result& r = results[v];
     r.block = block;
     r.blocks_per_sm = bps;
+    r.persistent = mode;
+    r.pad = 0;
     r.regs = 0;
     r.resident_blocks = 0;
-    integrate_variant_regs(v, morse, &r.regs);
-    integrate_variant_occupancy(v, morse, &r.resident_blocks);
+    if (mode == 1) {
+      integrate_variant_regs(v, morse, &r.regs);
+      integrate_variant_occupancy(v, morse, &r.resident_blocks);
+    } else {
+      grouped_func_info(mode == 2 ? 3 : 6, morse, &r.regs, &r.resident_blocks);
+    }
     r.ms = ms;
     r.lane_steps_per_s = ms > 0.f ? (double)cnt[1] / (ms * 1e-3) : 0.0;
     if (r.lane_steps_per_s > best_rate) {
@@ -1041,16 +1052,17 @@ int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* in
     }
     *n_results = v + 1;
   }
-  // Shapes within 2 % of the fastest on the sample are a tie (the sample's
-  // attempt cap evens out trajectory lengths): the tie goes to the smallest
-  // block, which schedules the full workload's uneven lanes at the finest
-  // grain (measured on the full sweep: 64 x 1 at 22.25 s against 256 x 1 at
-  // 23.5 s, equal on the sample).
-  if (e == cudaSuccess && best_v >= 0) {
+  // Persistent shapes within 2 % of the fastest on the sample are a tie
+  // (the sample's attempt cap evens out trajectory lengths): the tie goes to
+  // the smallest block, which schedules the full workload's uneven lanes at
+  // the finest grain (measured on the full sweep: 64 x 1 at 22.25 s against
+  // 256 x 1 at 23.5 s, equal on the sample).  A lane-group launch wins only
+  // outright.
+  if (e == cudaSuccess && best_v >= 0 && results[best_v].persistent == 1) {
     for (int v = 0; v < *n_results; ++v) {
       const qcams_tune_result& r = results[v];
       const qcams_tune_result& b = results[best_v];
-      if (r.lane_steps_per_s >= 0.98 * best_rate &&
+      if (r.persistent == 1 && r.lane_steps_per_s >= 0.98 * best_rate &&
           (r.block < b.block || (r.block == b.block && r.blocks_per_sm < b.blocks_per_sm)))
         best_v = v;
     }
@@ -1062,9 +1074,9 @@ int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* in
   ctx->timed = false;
   if (e != cudaSuccess || best_v < 0) return QCAMS_E_CUDA;
   *best = *integ;
-  best->persistent = 1;
-  best->block = results[best_v].block;
-  best->blocks_per_sm = results[best_v].blocks_per_sm;
+  best->persistent = results[best_v].persistent;
+  best->block = results[best_v].persistent == 1 ? results[best_v].block : 0;
+  best->blocks_per_sm = results[best_v].persistent == 1 ? results[best_v].blocks_per_sm : 0;
   return QCAMS_OK;
 }
 

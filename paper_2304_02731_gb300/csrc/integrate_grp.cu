@@ -479,6 +479,24 @@ cudaError_t launch_grp(const SysSet& sys, const DevShape* shapes, const IntegPar
 
 }  // namespace
 
+cudaError_t grouped_func_info(int lanes, bool all_morse, int* regs, int* blocks_per_sm) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaErrorInvalidValue;
+#define QCAMS_GRP_INFO(M, G)                                                               \
+  e = cudaFuncGetAttributes(&a, k_integrate_grp<M, G>);                                    \
+  if (e == cudaSuccess)                                                                    \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_integrate_grp<M, G>, \
+                                                      kGrpBlock, 0)
+  if (lanes == 3) {
+    if (all_morse) { QCAMS_GRP_INFO(true, 3); } else { QCAMS_GRP_INFO(false, 3); }
+  } else if (lanes == 6) {
+    if (all_morse) { QCAMS_GRP_INFO(true, 6); } else { QCAMS_GRP_INFO(false, 6); }
+  }
+#undef QCAMS_GRP_INFO
+  if (e == cudaSuccess) *regs = a.numRegs;
+  return e;
+}
+
 cudaError_t launch_integrate_grouped(const SysSet& sys, const DevShape* shapes,
                                      const IntegParams& ip, const DevBatch& b, int lanes,
                                      unsigned long long* counters, cudaStream_t st,

@@ -68,6 +68,9 @@ cudaError_t launch_integrate_grouped(const SysSet& sys, const DevShape* shapes,
                                      unsigned long long* counters, cudaStream_t st,
                                      bool all_morse);
 
+// Registers per thread and resident blocks per SM of the lane-group kernel.
+cudaError_t grouped_func_info(int lanes, bool all_morse, int* regs, int* blocks_per_sm);
+
 // FP32 integrator with compensated state updates (integrate32.cu).
 cudaError_t launch_integrate32(const SysSet& sys, const DevShape* shapes, const IntegParams& ip,
                                const DevBatch& b, int persistent, Ctx& ctx, cudaStream_t st,

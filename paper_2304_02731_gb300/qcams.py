@@ -89,8 +89,8 @@ class RunStats(C.Structure):
 
 class TuneResult(C.Structure):
     _fields_ = [("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("regs", C.c_int32),
-                ("resident_blocks", C.c_int32), ("ms", C.c_double),
-                ("lane_steps_per_s", C.c_double)]
+                ("resident_blocks", C.c_int32), ("persistent", C.c_int32), ("pad", C.c_int32),
+                ("ms", C.c_double), ("lane_steps_per_s", C.c_double)]
 
 
 class CMLP(C.Structure):
@@ -451,8 +451,9 @@ def fma_peak(precision: int = 64, stream=None) -> float:
 
 
 def autotune(systems, sample: Batch, integ: Integ, max_attempts: int = 1500, stream=None):
-    """qcams_autotune: measure every launch shape on an initialised sample
-    batch; returns (best Integ, list of per-variant result dicts)."""
+    """qcams_autotune: measure every launch (the persistent shapes and the
+    three- and six-lane groups) on an initialised sample batch; returns (best
+    Integ, list of per-launch result dicts)."""
     arr = systems_array(systems)
     res = (TuneResult * 16)()
     nres = C.c_int32()
@@ -460,8 +461,9 @@ def autotune(systems, sample: Batch, integ: Integ, max_attempts: int = 1500, str
     _check(lib().qcams_autotune(arr, len(systems), C.byref(integ), C.byref(sample.c),
                                 int(max_attempts), res, C.byref(nres), C.byref(best),
                                 _stream(stream)), "qcams_autotune")
-    out = [dict(block=r.block, blocks_per_sm=r.blocks_per_sm, regs=r.regs,
-                resident_blocks=r.resident_blocks, ms=r.ms, lane_steps_per_s=r.lane_steps_per_s)
+    out = [dict(block=r.block, blocks_per_sm=r.blocks_per_sm, persistent=r.persistent,
+                regs=r.regs, resident_blocks=r.resident_blocks, ms=r.ms,
+                lane_steps_per_s=r.lane_steps_per_s)
            for r in res[:nres.value]]
     return best, out
 
