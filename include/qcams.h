@@ -146,7 +146,7 @@ typedef struct {
                           2 = three lanes per trajectory, 3 = six lanes
                           per trajectory (FP64 adaptive steps only, else
                           QCAMS_E_INVALID; block and blocks_per_sm are not
-                          used): a step takes about 2.6x (3x) fewer
+                          used): a step takes about 2.8x (3.4x) fewer
                           warp-wide FP64 instructions, for batches too
                           small to fill the GPU (below ~10,000
                           trajectories); a warp holds 10 (5) trajectories

@@ -16,12 +16,12 @@
 // the matching velocities and stage accelerations) and evaluates the force
 // of pair c mod 3 (AB, BC, CA) of its lane index c.
 //   G = 3: lane j holds component j of both Jacobi vectors; a step takes
-//          about 195 warp-wide FP64 instructions, 10 trajectories a warp.
+//          183 warp-wide FP64 instructions, 10 trajectories a warp.
 //   G = 6: lane c holds one component (c < 3: rho1, else rho2), the two
-//          halves of the group evaluate the three pair forces twice; about
-//          160 instructions a step, 5 trajectories a warp.
-// The group exchanges the squared pair components, the pair force factors
-// and the error norm's partial sums by warp shuffles.  Large batches belong
+//          halves of the group evaluate the three pair forces twice; 152
+//          instructions a step, 5 trajectories a warp.
+// The group exchanges pair-vector components, the pair force factors and
+// the error norm's partial sums by warp shuffles.  Large batches belong
 // to the one-thread kernels, which carry 32 trajectories a warp.
 //
 // Every quantity the step control and the stop rules decide on (error norm,
@@ -94,11 +94,11 @@ __device__ __forceinline__ long long grp_max(long long v, int base) {
 // vectors are those of accel() in integrate.cu:
 //   r_AB = rho1,  r_BC = rho2 - cB rho1,  r_CA = rho2 + cA rho1.
 // Each lane forms component j of the three pair vectors (with G = 6, from
-// its own component and its partner's across the two halves), gathers the
-// three squared components of pair j from the lanes holding components
-// j+1, j+2 of its half (each sender choosing the square its receiver
-// needs), evaluates u_j = V'(r_j)/r_j, and the group exchanges
-// f_j = kf u_j and h_j = kh u_j.
+// its own component and its partner's across the two halves), gathers
+// components j+1, j+2 of pair j's vector from the lanes holding them in its
+// half (each sender choosing the pair its receiver needs), forms the
+// squared distance with one multiply and two FMAs, evaluates
+// u_j = V'(r_j)/r_j, and the group exchanges f_j = kf u_j and h_j = kh u_j.
 template <bool MORSE, int G>
 __device__ __forceinline__ void accel_grp(const DevSys& S, const Grp<G>& L,
                                           const double* __restrict__ T, const double* x,
@@ -113,17 +113,18 @@ __device__ __forceinline__ void accel_grp(const DevSys& S, const Grp<G>& L,
     x2 = L.c < 3 ? other : x[0];
   }
   const double rab = x1, rbc = fma(-S.cB, x1, x2), rca = fma(S.cA, x1, x2);
-  const double q0 = rab * rab, q1 = rbc * rbc, q2 = rca * rca;
-  double s = L.j == 0 ? q0 : (L.j == 1 ? q1 : q2);
   const int half = L.base + (L.c - L.j);   // lane of component 0 in this lane's half
+  double rk[2];
 #pragma unroll
   for (int r = 1; r <= 2; ++r) {
     // in round r a lane receives from the lane of component (j + r) mod 3,
-    // which sends its square of pair (its j - r) mod 3: the receiver's pair
+    // which sends its component of pair (its j - r) mod 3: the receiver's pair
     const int want = (L.j + 3 - r) % 3;
-    const double v = want == 0 ? q0 : (want == 1 ? q1 : q2);
-    s += __shfl_sync(FULL, v, half + (L.j + r) % 3);
+    const double v = want == 0 ? rab : (want == 1 ? rbc : rca);
+    rk[r - 1] = __shfl_sync(FULL, v, half + (L.j + r) % 3);
   }
+  const double rj = L.j == 0 ? rab : (L.j == 1 ? rbc : rca);
+  const double s = fma(rj, rj, fma(rk[0], rk[0], rk[1] * rk[1]));
   s_own = s;
   const double u = pair_u<MORSE>(L.q, s, T);
   const double f = L.kf * u, h = L.kh * u;
