@@ -389,9 +389,12 @@ int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys, const qcams_
  * itself when it is small; the integrator runs on it, from the same saved
  * initial state, with at most `max_attempts` step attempts per lane, once
  * for every supported (block, blocks_per_sm) variant of the persistent
- * launch and once for each lane-group launch (persistent = 2 and 3, one
- * warp per block), and the attempted lane-steps per second are measured
- * with CUDA events.  The sample's state is restored afterwards.  results
+ * launch and, when the sample has no more lanes than one warp per SM
+ * sub-partition (SM count x 128), once for each lane-group launch
+ * (persistent = 2 and 3, one warp per block); the attempted lane-steps per
+ * second are measured with CUDA events.  (With more lanes the persistent
+ * queue's refill matters, which a capped sample cannot show for the
+ * lane-group kernels.)  The sample's state is restored afterwards.  results
  * (host, room for QCAMS_TUNE_MAX_VARIANTS entries) receives one entry per
  * launch, *n_results their number, and *best a copy of *integ with the
  * fastest launch (its persistent, block and blocks_per_sm).  Persistent

@@ -1008,9 +1008,16 @@ int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* in
   IntegParams tip = ip;
   if (tip.max_steps > max_attempts) tip.max_steps = max_attempts;
   const bool morse = integrate_all_morse(ss);
-  // the persistent shapes, then the two lane-group launches
+  // The persistent shapes, then, for a sample with no more lanes than one
+  // warp per SM sub-partition, the two lane-group launches.  With more
+  // lanes the persistent queue's refill matters, and the attempt cap, which
+  // evens out trajectory lengths, hides the lane-group kernels' tails (a
+  // warp runs until its longest trajectory ends): on the sweep's
+  // 98,304-lane sample the three-lane launch measured level with the best
+  // shape and then ran the full sweep at half its rate.
   const int nv_shapes = integrate_variant_count();
-  const int nv = nv_shapes + 2;
+  const bool small = n <= (int64_t)ctx->sm_count * 4 * 32;
+  const int nv = nv_shapes + (small ? 2 : 0);
   int best_v = -1;
   double best_rate = -1.0;
   for (int v = 0; v < nv && v < QCAMS_TUNE_MAX_VARIANTS && e == cudaSuccess; ++v) {
