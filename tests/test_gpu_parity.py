@@ -590,6 +590,16 @@ def test_autotune_restores_sample_and_shapes_agree(Q):
     for k in ["y", "t", "h", "status", "nsteps", "nrej"]:
         assert np.array_equal(before[k], after[k]), k
     outs = []
+    # a sample larger than one warp per SM sub-partition (SM count x 128):
+    # the lane-group launches are not candidates (their tails, which the
+    # attempt cap hides, dominate full runs of large batches)
+    big = W.sweep_h2_ca(per_cell=53)
+    bb = Q.Batch.empty(big.n, "cuda", sys_id=big.sys_id, cell=big.cell, keep_u=False)
+    Q.init_states(big.systems, bb, big.E, big.b, big.v, big.j, big.R0, big.seed)
+    best_big, table_big = Q.autotune(big.systems, bb, integ, max_attempts=50)
+    assert big.n > Q.device_info()[0] * 128
+    assert len(table_big) == 6 and best_big.persistent == 1
+    del bb
     for block, bps in [(128, 1), (64, 1), (64, 6), (256, 1)]:
         it = Q.make_integ(**wl.integ, persistent=True, block=block, blocks_per_sm=bps)
         b2, hist, _, _ = Q.run_workload(wl, it, finalize=False)
