@@ -390,11 +390,12 @@ int qcams_run_batch_noalloc(const qcams_system* sys, int32_t n_sys, const qcams_
  * initial state, with at most `max_attempts` step attempts per lane, once
  * for every supported (block, blocks_per_sm) variant of the persistent
  * launch and, when the sample has no more lanes than one warp per SM
- * sub-partition (SM count x 128), once for each lane-group launch
+ * sub-partition (SM count x 128) or max_attempts is not below
+ * integ->max_steps (an uncapped run), once for each lane-group launch
  * (persistent = 2 and 3, one warp per block); the attempted lane-steps per
- * second are measured with CUDA events.  (With more lanes the persistent
- * queue's refill matters, which a capped sample cannot show for the
- * lane-group kernels.)  The sample's state is restored afterwards.  results
+ * second are measured with CUDA events.  (A larger capped sample cannot
+ * show the lane-group kernels' tails: their warps run until their longest
+ * trajectory ends, without refill.)  The sample's state is restored afterwards.  results
  * (host, room for QCAMS_TUNE_MAX_VARIANTS entries) receives one entry per
  * launch, *n_results their number, and *best a copy of *integ with the
  * fastest launch (its persistent, block and blocks_per_sm).  Persistent

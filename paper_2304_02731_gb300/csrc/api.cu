@@ -1008,16 +1008,17 @@ int qcams_autotune(const qcams_system* sys, int32_t n_sys, const qcams_integ* in
   IntegParams tip = ip;
   if (tip.max_steps > max_attempts) tip.max_steps = max_attempts;
   const bool morse = integrate_all_morse(ss);
-  // The persistent shapes, then, for a sample with no more lanes than one
-  // warp per SM sub-partition, the two lane-group launches.  With more
-  // lanes the persistent queue's refill matters, and the attempt cap, which
+  // The persistent shapes, then the two lane-group launches if the sample
+  // has no more lanes than one warp per SM sub-partition or the attempts
+  // are not capped below the run's own limit.  Otherwise the cap, which
   // evens out trajectory lengths, hides the lane-group kernels' tails (a
   // warp runs until its longest trajectory ends): on the sweep's
   // 98,304-lane sample the three-lane launch measured level with the best
   // shape and then ran the full sweep at half its rate.
   const int nv_shapes = integrate_variant_count();
   const bool small = n <= (int64_t)ctx->sm_count * 4 * 32;
-  const int nv = nv_shapes + (small ? 2 : 0);
+  const bool uncapped = max_attempts >= ip.max_steps;
+  const int nv = nv_shapes + ((small || uncapped) ? 2 : 0);
   int best_v = -1;
   double best_rate = -1.0;
   for (int v = 0; v < nv && v < QCAMS_TUNE_MAX_VARIANTS && e == cudaSuccess; ++v) {

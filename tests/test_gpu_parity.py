@@ -600,6 +600,16 @@ def test_autotune_restores_sample_and_shapes_agree(Q):
     assert big.n > Q.device_info()[0] * 128
     assert len(table_big) == 6 and best_big.persistent == 1
     del bb
+    # uncapped on 20,000 plain-study lanes, whose time the few long-lived
+    # complexes set: the lane-group launches are measured and one wins
+    pl = W.plain_h2_ca(per_b=4000)
+    pb = Q.Batch.empty(pl.n, "cuda", sys_id=pl.sys_id, cell=pl.cell, keep_u=False)
+    Q.init_states(pl.systems, pb, pl.E, pl.b, pl.v, pl.j, pl.R0, pl.seed)
+    pinteg = Q.make_integ(**pl.integ, persistent=True)
+    best_pl, table_pl = Q.autotune(pl.systems, pb, pinteg, max_attempts=pinteg.max_steps)
+    assert pl.n > Q.device_info()[0] * 128
+    assert len(table_pl) == 8 and best_pl.persistent in (2, 3)
+    del pb
     for block, bps in [(128, 1), (64, 1), (64, 6), (256, 1)]:
         it = Q.make_integ(**wl.integ, persistent=True, block=block, blocks_per_sm=bps)
         b2, hist, _, _ = Q.run_workload(wl, it, finalize=False)
