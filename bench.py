@@ -61,7 +61,7 @@ KERNEL_SOURCES = {
     32: ["integrate32.cu", "dp5_tableau.cuh"],
 }
 COUNTS_SOURCE_SHA256 = {
-    64: "16a68fcc4e943e7a5d29d7c3004ce0822648460446996eacf1011d7c6045fa07",
+    64: "130d7d1db1e117053912a66c771d9e78751bcc0dba47250e833458f06a8fefb4",
     32: "70e2932855a88f714f4f7b48b180d82a8b03cd6726c5035bdfd2c9d94b9bb1c1",
 }
 # DRAM bytes per trajectory of the integrator: ncu dram__bytes_read.sum +
